@@ -1,0 +1,330 @@
+"""Benchmark: BP message updates/s on the SmartFL-shaped 200k-variable graph.
+
+One step = one whole run of the hot path on one graph: messages reset to
+uniform, then TOPO_FB sweeps (forward levels then backward levels of the
+dependency analysis) until the largest message change is below 1e-6 or 100
+sweeps, then the marginals (Eq. 3) into a device buffer.  `value` counts the
+factor-to-variable message updates of the step over its device time (CUDA
+events on the library's stream), graph already resident in HBM.  The L2 is
+flushed (a 512 MiB write) between timed steps because the graph (~45 MiB of
+device data) fits in the 126 MiB L2.
+
+`e2e` times the same work through the C ABI from host buffers: graph creation
+(CSR transpose, host-to-device copies), schedule construction (Algorithm 2 on
+the host), the run, and the marginals copied back to the host.
+
+`--impl reference` times the FP64 oracle (the CPU baseline) on the host cores.
+`--gpus N` under torchrun runs one independent replica per GPU (a single graph
+does not shard); value is the sum over ranks of updates / the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, strategy, max_iters, tol, description)
+    "smartfl200k": ("smartfl", "TOPO_FB", 100, 1e-6,
+                    "SmartFL-shaped layered DAG: 200k vars in 200 layers, 300k factors, 5% evidence; "
+                    "TOPO_FB to max change < 1e-6 or 100 sweeps"),
+    "bingo1m": ("bingo", "PARALL", 500, 1e-6,
+                "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
+                "PARALL to max change < 1e-6 or 500 iterations"),
+    "tiny": ("tiny", "PARALL", 50, 0.0, "tiny derivation DAG, PARALL, exactly 50 iterations"),
+}
+
+
+def make_graph(name):
+    from paper_2509_22337_gb300 import gen
+    kind = WORKLOADS[name][0]
+    return {"smartfl": gen.smartfl, "bingo": gen.bingo, "tiny": gen.tiny}[kind]()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes_per_sweep(g):
+    """Bytes one full pass over every edge must move in the level kernel (see
+    the roofline section of the design notes): per edge the level entry and the
+    old and new message (12 B), per incidence read while forming v->a messages
+    the edge id, its level and its message (12 B), and per factor/variable
+    row headers and unary potentials."""
+    E, V, A = g.n_edges, g.n_vars, g.n_factors
+    return 12 * E + 12 * E + 12 * V + 13 * A
+
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__ as ge
+    from paper_2509_22337_gb300 import fbp as F
+
+    if rank == 0 or not os.path.exists(F.lib_path()):
+        ge.build()
+    if world > 1:
+        torch.distributed.barrier()
+    F.load()
+    _, strategy, max_iters, tol, desc = WORKLOADS[args.workload]
+    g = make_graph(args.workload)
+    stream = torch.cuda.current_stream()
+    G = F.Graph(g, strategy, stream=stream)
+    p_out = torch.empty(max(g.n_vars, 1), dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        G.reset()
+        G.run(max_iters, tol)
+        G.marginals(out=p_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    updates = 0
+    launches = 0
+    run_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            st = G.stats()
+            updates += st["updates"]
+            launches += st["kernel_launches"] + 2  # + reset fill + marginals
+            run_ms.append(st["run_ms"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(ms))
+    st = G.stats()
+    t_max = total_ms
+    tot_updates = updates
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([float(updates)], device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tot_updates = u.item()
+    value = tot_updates / (t_max / 1e3)
+
+    # roofline of the dominant kernel: one level launch per level per half
+    sweeps = st["iters"]
+    level_launches = st["kernel_launches"]
+    kernel_ms = float(np.median(run_ms))
+    per_launch_ms = kernel_ms / max(level_launches, 1)
+    bytes_per_launch = algorithmic_bytes_per_sweep(g) * 2 * sweeps / max(level_launches, 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_level_edges", "per_launch_us": round(per_launch_ms * 1e3, 3),
+            "bytes_per_launch": int(bytes_per_launch), "peak_source": "measured" if os.path.exists(
+                os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"}
+
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if rank == 0 or True:
+        fp = np.ascontiguousarray(g.factor_ptr, np.int64)
+        host_p = np.empty(g.n_vars, np.float32)
+        e2e_t = []
+        h2d = d2h = 0
+        for i in range(max(2, min(args.steps, 5))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H = F.Graph(g, strategy, stream=stream)
+            H.run(max_iters, tol)
+            host_p[:] = H.marginals()
+            sth = H.stats()
+            H.close()
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+        E, V, A = g.n_edges, g.n_vars, g.n_factors
+        halves = 2 if strategy == "TOPO_FB" else 1
+        h2d = 4 * (A + 1) + A + 4 * A + 4 * E * 3 + 4 * (V + 1) + 4 * V + (8 * E * halves if strategy != "PARALL" else 0)
+        d2h = 4 * V + 4 * 64 * sth["iters"] + 8
+        e2e = {"value": round(sth["updates"] / float(np.median(e2e_t)), 1), "unit": "msg_updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(float(np.median(e2e_t)) * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "BP message updates/s", "value": round(value, 1), "unit": "msg_updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "n_vars": g.n_vars, "n_factors": g.n_factors,
+                       "n_edges": g.n_edges, "strategy": strategy, "max_iters": max_iters, "tol": tol,
+                       "sweeps_per_step": st["iters"], "levels_per_sweep": st["levels"],
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "time_to_converge_ms": round(total_ms / args.steps, 4),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    G.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(workload, budget_s=15.0, impl_line=False):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    the first few sweeps/iterations of the same graph and schedule."""
+    from oracle import oracle as O
+    O.build()
+    _, strategy, max_iters, tol, _ = WORKLOADS[workload]
+    g = make_graph(workload)
+    o = O.Oracle(g)
+    # calibrate: one iteration
+    t0 = time.perf_counter()
+    r = o.run(strategy, 1, 0.0)
+    t1 = time.perf_counter() - t0
+    iters = int(max(1, min(max_iters, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    r = o.run(strategy, iters, 0.0)
+    dt = time.perf_counter() - t0
+    return {"value": round(r["updates"] / dt, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {strategy} on the "
+                      f"full {workload} graph from uniform messages ({dt:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    _, strategy, max_iters, tol, desc = WORKLOADS[args.workload]
+    g = make_graph(args.workload)
+    o = O.Oracle(g)
+    sample_iters = {"smartfl200k": 4, "bingo1m": 2, "tiny": 50}[args.workload]
+    for _ in range(args.warmup):
+        o.run(strategy, 1, 0.0)
+    times, upd = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = o.run(strategy, sample_iters, 0.0)
+        times.append(time.perf_counter() - t0)
+        upd += r["updates"]
+    tot = float(sum(times))
+    value = upd / tot
+    line = {
+        "impl": "reference", "metric": "BP message updates/s", "value": round(value, 1),
+        "unit": "msg_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n_vars": g.n_vars, "n_edges": g.n_edges,
+                   "strategy": strategy, "sample": f"{sample_iters} sweeps per step"},
+        "cpu_baseline": {"value": round(value, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_iters} {strategy} sweeps of the full graph per step"},
+        "e2e": {"value": round(value, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="smartfl200k", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -560,7 +560,14 @@ typedef struct {
     double *v2a, *newm, *scratch, *mu;
     int64_t *fstamp, *vstamp, stamp;
     double *dres;   /* optional: per-edge |delta m1| of the last write */
+    double min_pos; /* diagnostic: smallest nonzero entry of any written message */
 } run_ws;
+
+static void note_min(run_ws *ws, const double *m)
+{
+    if (m[0] > 0.0 && m[0] < ws->min_pos) ws->min_pos = m[0];
+    if (m[1] > 0.0 && m[1] < ws->min_pos) ws->min_pos = m[1];
+}
 
 static void run_levels(const og_graph *g, double *a2v, int64_t k, const int64_t *level_ptr,
                        const int32_t *level_edges, run_ws *ws, double *residual, int64_t *guards)
@@ -591,6 +598,7 @@ static void run_levels(const og_graph *g, double *a2v, int64_t k, const int64_t 
             double d = fabs(ws->newm[2 * (i - lo) + 1] - a2v[2 * e + 1]);
             if (d > *residual) *residual = d;
             if (ws->dres) ws->dres[e] = d;
+            note_min(ws, ws->newm + 2 * (i - lo));
             a2v[2 * e] = ws->newm[2 * (i - lo)];
             a2v[2 * e + 1] = ws->newm[2 * (i - lo) + 1];
         }
@@ -629,6 +637,7 @@ static void run_def2(const og_graph *g, double *a2v, const int64_t *rank, const 
         *guards += a2v_alg1(g, ws->v2a, e, out, ws->mu);
         double d = fabs(out[1] - oldm[2 * e + 1]);
         if (d > *residual) *residual = d;
+        note_min(ws, out);
         a2v[2 * e] = out[0]; a2v[2 * e + 1] = out[1];
     }
 }
@@ -672,11 +681,13 @@ static int64_t residual_active(const og_graph *g, const double *dres, double tol
 /* max_iters (returns 1).  TOPO_FB runs the forward then the backward        */
 /* levels in one iteration.  def2 = 1 executes Definition 2 directly instead */
 /* of the levels.  res_hist (optional) receives each iteration's residual;   */
-/* updates_out (optional) the number of a->v writes.                         */
+/* updates_out (optional) the number of a->v writes; min_pos_out (optional)  */
+/* the smallest nonzero entry of any message written (a range diagnostic:    */
+/* it tells whether the run stayed within single-precision range).           */
 /* ------------------------------------------------------------------------ */
 int orc_run(og_graph *g, int strategy, const int64_t *custom, int max_iters, double tol,
             int def2, int init, double *a2v, int32_t *iters_out, double *residual_out,
-            double *res_hist, int64_t *guards_out, int64_t *updates_out)
+            double *res_hist, int64_t *guards_out, int64_t *updates_out, double *min_pos_out)
 {
     int64_t E = g->ne;
     int64_t maxd = 1;
@@ -687,6 +698,7 @@ int orc_run(og_graph *g, int strategy, const int64_t *custom, int max_iters, dou
         if (g->fptr[a + 1] - g->fptr[a] > bmax) bmax = (int)(g->fptr[a + 1] - g->fptr[a]);
     run_ws ws;
     memset(&ws, 0, sizeof(ws));
+    ws.min_pos = 1.0;
     ws.v2a = (double *)malloc(sizeof(double) * 2 * (E + 1));
     ws.newm = (double *)malloc(sizeof(double) * 2 * (E + 1));
     ws.scratch = (double *)malloc(sizeof(double) * 4 * (maxd + 2));
@@ -763,6 +775,7 @@ int orc_run(og_graph *g, int strategy, const int64_t *custom, int max_iters, dou
     if (iters_out) *iters_out = it;
     if (residual_out) *residual_out = res;
 done:
+    if (min_pos_out) *min_pos_out = ws.min_pos;
     if (guards_out) *guards_out = guards;
     if (updates_out) *updates_out = updates;
     free(ws.v2a); free(ws.newm); free(ws.scratch); free(ws.mu); free(ws.fstamp); free(ws.vstamp);

@@ -75,7 +75,8 @@ def lib():
             L.orc_in_ne.restype = C.c_int
             L.orc_run.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                   C.c_int, _f64, C.POINTER(C.c_int32), C.POINTER(C.c_double),
-                                  C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+                                  C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double)]
             L.orc_run.restype = C.c_int
             L.orc_marginals.argtypes = [C.c_void_p, _f64, _f64]
             L.orc_marginals.restype = C.c_int64
@@ -170,16 +171,17 @@ class Oracle:
                 else np.zeros(2 * self.n_edges + 2, dtype=np.float64))
         if msgs.shape[0] < 2 * self.n_edges + 2:
             msgs = np.concatenate([msgs, np.zeros(2 * self.n_edges + 2 - msgs.shape[0])])
-        it, res, gd, up = C.c_int32(), C.c_double(), C.c_int64(), C.c_int64()
+        it, res, gd, up, mp = C.c_int32(), C.c_double(), C.c_int64(), C.c_int64(), C.c_double()
         hist = np.zeros(max(max_iters, 1), dtype=np.float64) if history else None
         cbuf = None if custom is None else np.ascontiguousarray(custom, np.int64)
         rc = lib().orc_run(self._h, s, None if cbuf is None else cbuf.ctypes.data, int(max_iters),
                            float(tol), int(def2), int(init), msgs, C.byref(it), C.byref(res),
-                           None if hist is None else hist.ctypes.data, C.byref(gd), C.byref(up))
+                           None if hist is None else hist.ctypes.data, C.byref(gd), C.byref(up),
+                           C.byref(mp))
         if rc < 0:
             raise ValueError(f"oracle run failed ({rc})")
         out = dict(converged=rc == 0, iters=int(it.value), residual=float(res.value),
-                   guards=int(gd.value), updates=int(up.value),
+                   guards=int(gd.value), updates=int(up.value), min_pos=float(mp.value),
                    a2v=msgs[: 2 * self.n_edges].reshape(-1, 2).copy())
         if hist is not None:
             out["res_hist"] = hist[: out["iters"]].copy()

@@ -1,0 +1,661 @@
+// Host side of the belief-propagation library: the C ABI of include/fbp.h,
+// graph ingest and layout (Sec. 4.1 "Initialization", Sec. 4.3.2), update
+// strategy -> ranks (Table 1, Definition 2), the dependency analysis of
+// Algorithm 2 (Sec. 4.2.3) and the iteration driver (Sec. 4.1 "Kernel
+// Launch" / "Message Passing").
+#include "fbp.h"
+#include "fbp_internal.h"
+#include "fbp_sched.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+using namespace fbp;
+
+namespace {
+thread_local std::string t_err;
+}  // namespace
+
+int fbp::fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+namespace {
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return fail(FBP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));       \
+    } while (0)
+
+// rho encoding of a normalised pair computed in double, rounded once.
+float enc_host(double m0, double m1)
+{
+    if (!(m0 + m1 > 0.0)) return 1.0f;
+    if (m1 >= m0) return (float)(m0 / m1);
+    float r = (float)(m1 / m0);
+    return -r;  // -0.0f for the hard message (1, 0)
+}
+
+float phi_of(float prior, int8_t ev)
+{
+    if (ev == 0) return -0.0f;
+    if (ev == 1) return 0.0f;
+    if (!std::isnan(prior)) return enc_host(1.0 - (double)prior, (double)prior);
+    return 1.0f;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// graph handle
+// ---------------------------------------------------------------------------
+struct LevelSet {                    // one level list (one half of TOPO_FB)
+    std::vector<int64_t> lp;         // level_ptr
+    std::vector<int32_t> le;         // level_edges (canonical order)
+    int32_t *d_le = nullptr;         // device copy of le
+    int32_t *d_vlev = nullptr;       // [E] var-major level index of each edge
+};
+
+struct fbp_graph {
+    HostCSR h;                        // host CSR + transpose (also used by scheduling)
+    std::vector<float> prior;
+    std::vector<int8_t> evidence;
+    std::vector<float> phi;           // rho-encoded unary potentials
+    DevGraph d;
+    cudaStream_t stream = nullptr;
+    fbp_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> owned;
+    // messages
+    float *a2v[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *v2a = nullptr;
+    float *pairs = nullptr;           // export/import staging [2E]
+    float *p1 = nullptr;              // marginals [V]
+    // schedule
+    int strategy = FBP_PARALL;
+    std::vector<LevelSet> halves;     // 1 (static) or 2 (TOPO_FB)
+    // residual strategy working state
+    float *dres = nullptr;            // [E] |delta m1| of the last write
+    int32_t *d_act = nullptr;         // [E] active edges (residual)
+    // per-iteration control
+    unsigned *d_res = nullptr;
+    unsigned long long *d_guards = nullptr;
+    unsigned *h_res = nullptr;        // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    fbp_stats stats{};
+};
+
+namespace {
+
+int dalloc(fbp_graph *g, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (g->has_alloc) {
+        *p = g->alloc.alloc(bytes, g->alloc.ctx);
+        if (!*p) return fail(FBP_ERR_OOM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return fail(FBP_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    g->owned.push_back(*p);
+    return FBP_OK;
+}
+
+template <class T>
+int dalloc_n(fbp_graph *g, T **p, size_t n)
+{
+    return dalloc(g, (void **)p, n * sizeof(T));
+}
+
+template <class T>
+int upload(fbp_graph *g, T **p, const T *src, size_t n)
+{
+    int rc = dalloc_n(g, p, n);
+    if (rc) return rc;
+    if (n) CUDA_TRY(cudaMemcpyAsync(*p, src, n * sizeof(T), cudaMemcpyHostToDevice, g->stream));
+    return FBP_OK;
+}
+
+void dfree(fbp_graph *g, void *p)
+{
+    if (!p) return;
+    auto it = std::find(g->owned.begin(), g->owned.end(), p);
+    if (it != g->owned.end()) g->owned.erase(it);
+    if (g->has_alloc) g->alloc.free(p, g->alloc.ctx);
+    else cudaFree(p);
+}
+
+void free_levels(fbp_graph *g)
+{
+    for (auto &ls : g->halves) {
+        dfree(g, ls.d_le);
+        dfree(g, ls.d_vlev);
+    }
+    g->halves.clear();
+}
+
+// Upload one level list and the var-major level index of every edge.
+int upload_levels(fbp_graph *g, LevelSet &ls)
+{
+    const HostCSR &h = g->h;
+    std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max());
+    for (size_t L = 0; L + 1 < ls.lp.size(); ++L)
+        for (int64_t i = ls.lp[L]; i < ls.lp[L + 1]; ++i) elev[ls.le[i]] = (int32_t)L;
+    std::vector<int32_t> vlev(h.ne);
+    for (int32_t k = 0; k < h.ne; ++k) vlev[k] = elev[h.vedge[k]];
+    int rc = upload(g, &ls.d_le, ls.le.data(), ls.le.size());
+    if (!rc) rc = upload(g, &ls.d_vlev, vlev.data(), vlev.size());
+    return rc;
+}
+
+int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
+                     const uint8_t *ftype, const float *fparam, const float *prior,
+                     const int8_t *evidence)
+{
+    if (nv < 0 || na < 0) return fail(FBP_ERR_INVALID_ARG, "negative size");
+    if (!fptr) return fail(FBP_ERR_INVALID_ARG, "factor_ptr is NULL");
+    if (fptr[0] != 0) return fail(FBP_ERR_INVALID_ARG, "factor_ptr[0] != 0");
+    for (int32_t a = 0; a < na; ++a)
+        if (fptr[a + 1] < fptr[a]) return fail(FBP_ERR_INVALID_ARG, "factor_ptr decreases at %d", a);
+    const int64_t E = fptr[na];
+    if (E >= (int64_t)1 << 31) return fail(FBP_ERR_INVALID_ARG, "too many edges (%lld)", (long long)E);
+    if (E > 0 && !fvars) return fail(FBP_ERR_INVALID_ARG, "factor_vars is NULL");
+    if (na > 0 && (!ftype || !fparam)) return fail(FBP_ERR_INVALID_ARG, "factor_type/param NULL");
+    std::vector<int32_t> seen((size_t)nv, -1);
+    for (int32_t a = 0; a < na; ++a) {
+        const int64_t lo = fptr[a], n = fptr[a + 1] - lo;
+        for (int64_t e = lo; e < lo + n; ++e) {
+            int32_t v = fvars[e];
+            if (v < 0 || v >= nv) return fail(FBP_ERR_INVALID_ARG, "factor %d: variable %d out of range", a, v);
+            if (seen[v] == a) return fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, v);
+            seen[v] = a;
+        }
+        const int t = ftype[a];
+        const float p = fparam[a];
+        bool ok;
+        switch (t) {
+        case FBP_AND: case FBP_OR: case FBP_NOISY_IMPLY: case FBP_NOISY_AND: ok = n >= 2; break;
+        case FBP_NOT: ok = n == 2; break;
+        case FBP_EQ: ok = n >= 1; break;
+        case FBP_PRIOR: ok = n == 1; break;
+        default: return fail(FBP_ERR_INVALID_ARG, "factor %d: unknown type %d", a, t);
+        }
+        if (!ok) return fail(FBP_ERR_INVALID_ARG, "factor %d: arity %lld invalid for type %d", a, (long long)n, t);
+        if ((t == FBP_NOISY_IMPLY || t == FBP_NOISY_AND || t == FBP_PRIOR) && !(p >= 0.f && p <= 1.f))
+            return fail(FBP_ERR_INVALID_ARG, "factor %d: parameter outside [0,1]", a);
+    }
+    if (prior)
+        for (int32_t v = 0; v < nv; ++v)
+            if (!std::isnan(prior[v]) && !(prior[v] >= 0.f && prior[v] <= 1.f))
+                return fail(FBP_ERR_INVALID_ARG, "prior of variable %d outside [0,1]", v);
+    if (evidence)
+        for (int32_t v = 0; v < nv; ++v)
+            if (evidence[v] < -1 || evidence[v] > 1)
+                return fail(FBP_ERR_INVALID_ARG, "evidence of variable %d not in {-1,0,1}", v);
+    return FBP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" const char *fbp_last_error(void) { return t_err.c_str(); }
+
+extern "C" void fbp_graph_destroy(fbp_graph *g)
+{
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    else cudaDeviceSynchronize();
+    std::vector<void *> all = g->owned;
+    for (void *p : all) dfree(g, p);
+    if (g->h_res) cudaFreeHost(g->h_res);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t *factor_ptr,
+                                const int32_t *factor_vars, const uint8_t *factor_type,
+                                const float *factor_param, const float *prior_p1,
+                                const int8_t *evidence, const fbp_allocator *alloc,
+                                void *cuda_stream, fbp_graph **out)
+{
+    t_err.clear();
+    if (!out) return fail(FBP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_graph_args(n_vars, n_factors, factor_ptr, factor_vars, factor_type, factor_param,
+                              prior_p1, evidence);
+    if (rc) return rc;
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(FBP_ERR_INVALID_ARG, "allocator incomplete");
+
+    fbp_graph *g = new fbp_graph();
+    g->stream = (cudaStream_t)cuda_stream;
+    if (alloc) {
+        g->alloc = *alloc;
+        g->has_alloc = true;
+    }
+    build_host_csr(n_vars, n_factors, factor_ptr, factor_vars, factor_type, factor_param, g->h);
+    const HostCSR &h = g->h;
+    g->prior.assign(prior_p1 ? prior_p1 : nullptr, prior_p1 ? prior_p1 + n_vars : nullptr);
+    if (!prior_p1) g->prior.assign(n_vars, std::numeric_limits<float>::quiet_NaN());
+    g->evidence.assign(evidence ? evidence : nullptr, evidence ? evidence + n_vars : nullptr);
+    if (!evidence) g->evidence.assign(n_vars, (int8_t)-1);
+    g->phi.resize(n_vars);
+    for (int32_t v = 0; v < n_vars; ++v) g->phi[v] = phi_of(g->prior[v], g->evidence[v]);
+
+    int32_t *fptr32 = nullptr, *fvars = nullptr, *efac = nullptr, *vptr = nullptr, *vedge = nullptr;
+    uint8_t *ftype = nullptr;
+    float *fparam = nullptr, *phi = nullptr;
+    std::vector<int32_t> fp32(h.fptr.begin(), h.fptr.end());
+    if ((rc = upload(g, &fptr32, fp32.data(), fp32.size())) ||
+        (rc = upload(g, &ftype, h.ftype.data(), h.ftype.size())) ||
+        (rc = upload(g, &fparam, h.fparam.data(), h.fparam.size())) ||
+        (rc = upload(g, &fvars, h.fvars.data(), h.fvars.size())) ||
+        (rc = upload(g, &efac, h.efac.data(), h.efac.size())) ||
+        (rc = upload(g, &vptr, h.vptr.data(), h.vptr.size())) ||
+        (rc = upload(g, &vedge, h.vedge.data(), h.vedge.size())) ||
+        (rc = upload(g, &phi, g->phi.data(), g->phi.size())) ||
+        (rc = dalloc_n(g, &g->a2v[0], (size_t)h.ne)) ||
+        (rc = dalloc_n(g, &g->d_res, (size_t)kResSlots)) ||
+        (rc = dalloc_n(g, &g->d_guards, 1))) {
+        std::string keep = t_err;
+        fbp_graph_destroy(g);
+        t_err = keep;
+        return rc;
+    }
+    g->d.nv = n_vars;
+    g->d.na = n_factors;
+    g->d.ne = h.ne;
+    g->d.fptr = fptr32;
+    g->d.ftype = ftype;
+    g->d.fparam = fparam;
+    g->d.fvars = fvars;
+    g->d.efac = efac;
+    g->d.vptr = vptr;
+    g->d.vedge = vedge;
+    g->d.phi = phi;
+    launch_fill(g->a2v[0], 1.0f, h.ne, g->stream);  // uniform initial messages
+    cudaError_t e = cudaMallocHost((void **)&g->h_res, sizeof(unsigned) * kResSlots);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fbp_graph_destroy(g);
+        return fail(FBP_ERR_CUDA, "graph setup: %s", cudaGetErrorString(e));
+    }
+    LevelSet ls;
+    ls.lp = {0, (int64_t)h.ne};
+    if (h.ne == 0) ls.lp = {0};
+    g->halves.push_back(std::move(ls));
+    g->strategy = FBP_PARALL;
+    *out = g;
+    return FBP_OK;
+}
+
+extern "C" int fbp_schedule_set(fbp_graph *g, const fbp_schedule_spec *spec)
+{
+    t_err.clear();
+    if (!g || !spec) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    const HostCSR &h = g->h;
+    std::vector<LevelSet> halves;
+    int s = spec->strategy;
+    if (s == FBP_RESIDUAL) {
+        if (spec->residual_buckets != 0 && spec->residual_buckets != 3)
+            return fail(FBP_ERR_INVALID_ARG, "residual_buckets must be 0 or 3");
+        LevelSet ls;  // iteration 1 is PARALL
+        ls.lp = {0, (int64_t)h.ne};
+        if (h.ne == 0) ls.lp = {0};
+        halves.push_back(std::move(ls));
+    } else {
+        int nh = s == FBP_TOPO_FB ? 2 : 1;
+        for (int b = 0; b < nh; ++b) {
+            std::vector<int64_t> rank;
+            int rc = build_ranks(h, *spec, b, rank);
+            if (rc) return rc;
+            LevelSet ls;
+            dependency_levels(h, rank.data(), nullptr, h.ne, ls.lp, ls.le);
+            halves.push_back(std::move(ls));
+        }
+    }
+    free_levels(g);
+    g->halves = std::move(halves);
+    g->strategy = s;
+    if (s != FBP_PARALL) {
+        for (auto &ls : g->halves) {
+            if (ls.le.empty() && h.ne) {  // PARALL list (RESIDUAL's first iteration)
+                ls.le.resize(h.ne);
+                for (int32_t e = 0; e < h.ne; ++e) ls.le[e] = e;
+            }
+            int rc = upload_levels(g, ls);
+            if (rc) return rc;
+        }
+        if (!g->a2v[1] && dalloc_n(g, &g->a2v[1], (size_t)h.ne)) return FBP_ERR_OOM;
+    }
+    if (s == FBP_RESIDUAL) {
+        if (!g->dres && dalloc_n(g, &g->dres, (size_t)h.ne)) return FBP_ERR_OOM;
+        if (!g->d_act && dalloc_n(g, &g->d_act, (size_t)h.ne)) return FBP_ERR_OOM;
+    }
+    return FBP_OK;
+}
+
+extern "C" int fbp_schedule_build_host(int32_t n_vars, int32_t n_factors, const int64_t *factor_ptr,
+                                       const int32_t *factor_vars, const fbp_schedule_spec *spec,
+                                       int32_t backward, int32_t *n_levels, int64_t *level_ptr,
+                                       int32_t *level_edges)
+{
+    t_err.clear();
+    if (!spec || !n_levels) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    if (n_vars < 0 || n_factors < 0 || !factor_ptr || factor_ptr[0] != 0)
+        return fail(FBP_ERR_INVALID_ARG, "bad CSR");
+    for (int32_t a = 0; a < n_factors; ++a)
+        if (factor_ptr[a + 1] < factor_ptr[a]) return fail(FBP_ERR_INVALID_ARG, "bad CSR");
+    const int64_t E = factor_ptr[n_factors];
+    if (E >= (int64_t)1 << 31) return fail(FBP_ERR_INVALID_ARG, "too many edges");
+    for (int64_t e = 0; e < E; ++e)
+        if (factor_vars[e] < 0 || factor_vars[e] >= n_vars) return fail(FBP_ERR_INVALID_ARG, "bad variable");
+    if (spec->strategy == FBP_RESIDUAL) return fail(FBP_ERR_INVALID_ARG, "RESIDUAL levels are dynamic");
+    HostCSR h;
+    std::vector<uint8_t> t(n_factors, 0);
+    std::vector<float> p(n_factors, 0.f);
+    build_host_csr(n_vars, n_factors, factor_ptr, factor_vars, t.data(), p.data(), h);
+    std::vector<int64_t> rank;
+    int rc = build_ranks(h, *spec, backward ? 1 : 0, rank);
+    if (rc) return rc;
+    std::vector<int64_t> lp;
+    std::vector<int32_t> le;
+    dependency_levels(h, rank.data(), nullptr, h.ne, lp, le);
+    *n_levels = (int32_t)(lp.size() - 1);
+    if (level_ptr) std::copy(lp.begin(), lp.end(), level_ptr);
+    if (level_edges) std::copy(le.begin(), le.end(), level_edges);
+    return FBP_OK;
+}
+
+extern "C" int fbp_schedule_levels(const fbp_graph *g, int32_t *n_levels, int64_t *level_ptr,
+                                   int32_t *level_edges)
+{
+    t_err.clear();
+    if (!g || !n_levels) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    int32_t k = 0;
+    for (auto &ls : g->halves) k += (int32_t)ls.lp.size() - 1;
+    *n_levels = k;
+    if (!level_ptr && !level_edges) return FBP_OK;
+    int64_t base = 0;
+    int32_t j = 0;
+    if (level_ptr) level_ptr[0] = 0;
+    for (auto &ls : g->halves) {
+        for (size_t L = 1; L < ls.lp.size(); ++L) {
+            if (level_ptr) level_ptr[++j] = base + ls.lp[L];
+        }
+        if (level_edges) {
+            if (!ls.le.empty()) std::copy(ls.le.begin(), ls.le.end(), level_edges + base);
+            else for (int32_t e = 0; e < g->h.ne; ++e) level_edges[base + e] = e;  // PARALL
+        }
+        base += ls.lp.back();
+    }
+    return FBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// iteration driver
+// ---------------------------------------------------------------------------
+namespace {
+
+int read_residual(fbp_graph *g, double *res)
+{
+    CUDA_TRY(cudaMemcpyAsync(g->h_res, g->d_res, sizeof(unsigned) * kResSlots, cudaMemcpyDeviceToHost,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    unsigned m = 0;
+    for (int i = 0; i < kResSlots; ++i) m = std::max(m, g->h_res[i]);
+    float f;
+    std::memcpy(&f, &m, sizeof f);
+    *res = (double)f;
+    return FBP_OK;
+}
+
+// One half-iteration over a level list; messages go from a2v[cur] to the
+// other buffer, then the buffers swap.
+void run_half(fbp_graph *g, const LevelSet &ls, IterCtl ctl)
+{
+    const float *cur = g->a2v[g->cur];
+    float *nxt = g->a2v[g->cur ^ 1];
+    for (size_t L = 0; L + 1 < ls.lp.size(); ++L) {
+        launch_level(g->d, ls.d_le + ls.lp[L], (int32_t)(ls.lp[L + 1] - ls.lp[L]), (int32_t)L, ls.d_vlev,
+                     cur, nxt, ctl, nullptr, g->stream);
+        g->stats.kernel_launches++;
+    }
+    g->cur ^= 1;
+}
+
+}  // namespace
+
+extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                       double *residual_out)
+{
+    t_err.clear();
+    if (!g || max_iters < 0 || !(tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
+    if (g->strategy == FBP_RESIDUAL) return fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
+    const HostCSR &h = g->h;
+    g->stats = fbp_stats{};
+    for (auto &ls : g->halves) g->stats.levels += (int32_t)ls.lp.size() - 1;
+    IterCtl ctl{g->d_res, g->d_guards};
+    CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
+    if (g->strategy == FBP_PARALL && !g->v2a) {
+        if (dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
+    }
+    CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
+    int32_t it = 0;
+    double res = 0.0;
+    int status = FBP_NOT_CONVERGED;
+    for (it = 1; it <= max_iters; ++it) {
+        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
+        if (g->strategy == FBP_PARALL) {
+            launch_v2a_flood(g->d, g->a2v[g->cur], g->v2a, g->stream);
+            launch_a2v_flood(g->d, g->v2a, g->a2v[g->cur], ctl, g->stream);
+            g->stats.kernel_launches += 2;
+            g->stats.updates += h.ne;
+        } else {
+            for (auto &ls : g->halves) {
+                run_half(g, ls, ctl);
+                g->stats.updates += h.ne;
+            }
+        }
+        CUDA_TRY(cudaGetLastError());
+        int rc = read_residual(g, &res);
+        if (rc) return rc;
+        if (res < tol) {
+            status = FBP_OK;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    CUDA_TRY(cudaEventRecord(g->ev1, g->stream));
+    CUDA_TRY(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    unsigned long long guards = 0;
+    CUDA_TRY(cudaMemcpy(&guards, g->d_guards, sizeof guards, cudaMemcpyDeviceToHost));
+    g->stats.iters = it;
+    g->stats.residual = res;
+    g->stats.run_ms = ms;
+    g->stats.guards = (int64_t)guards;
+    if (iters_out) *iters_out = it;
+    if (residual_out) *residual_out = res;
+    return status;
+}
+
+// RESIDUAL strategy (dynamic levels rebuilt every iteration on the host).
+int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                     double *residual_out)
+{
+    const HostCSR &h = g->h;
+    g->stats = fbp_stats{};
+    IterCtl ctl{g->d_res, g->d_guards};
+    CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
+    CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
+    std::vector<float> dres(h.ne);
+    std::vector<int64_t> rank(h.ne);
+    std::vector<int32_t> act;
+    int32_t it = 0;
+    double res = 0.0;
+    int status = FBP_NOT_CONVERGED;
+    LevelSet &ls = g->halves[0];
+    for (it = 1; it <= max_iters; ++it) {
+        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
+        int64_t n;
+        if (it == 1) {
+            std::fill(rank.begin(), rank.end(), 0);
+            act.resize(h.ne);
+            for (int32_t e = 0; e < h.ne; ++e) act[e] = e;
+            n = h.ne;
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(dres.data(), g->dres, sizeof(float) * h.ne, cudaMemcpyDeviceToHost,
+                                     g->stream));
+            CUDA_TRY(cudaStreamSynchronize(g->stream));
+            n = residual_classes(h, dres.data(), tol, rank.data(), act);
+        }
+        dependency_levels(h, rank.data(), act.data(), n, ls.lp, ls.le);
+        dfree(g, ls.d_le);
+        dfree(g, ls.d_vlev);
+        ls.d_le = nullptr;
+        ls.d_vlev = nullptr;
+        int rc = upload_levels(g, ls);
+        if (rc) return rc;
+        g->stats.levels = (int32_t)ls.lp.size() - 1;
+        // inactive edges keep their value: start the next buffer as a copy
+        CUDA_TRY(cudaMemcpyAsync(g->a2v[g->cur ^ 1], g->a2v[g->cur], sizeof(float) * h.ne,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+        CUDA_TRY(cudaMemsetAsync(g->dres, 0, sizeof(float) * h.ne, g->stream));
+        const float *cur = g->a2v[g->cur];
+        float *nxt = g->a2v[g->cur ^ 1];
+        IterCtl c2 = ctl;
+        for (size_t L = 0; L + 1 < ls.lp.size(); ++L) {
+            launch_level(g->d, ls.d_le + ls.lp[L], (int32_t)(ls.lp[L + 1] - ls.lp[L]), (int32_t)L,
+                         ls.d_vlev, cur, nxt, c2, g->dres, g->stream);
+            g->stats.kernel_launches++;
+        }
+        g->cur ^= 1;
+        g->stats.updates += n;
+        CUDA_TRY(cudaGetLastError());
+        rc = read_residual(g, &res);
+        if (rc) return rc;
+        if (res < tol) {
+            status = FBP_OK;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    CUDA_TRY(cudaEventRecord(g->ev1, g->stream));
+    CUDA_TRY(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    unsigned long long guards = 0;
+    CUDA_TRY(cudaMemcpy(&guards, g->d_guards, sizeof guards, cudaMemcpyDeviceToHost));
+    g->stats.iters = it;
+    g->stats.residual = res;
+    g->stats.run_ms = ms;
+    g->stats.guards = (int64_t)guards;
+    if (iters_out) *iters_out = it;
+    if (residual_out) *residual_out = res;
+    return status;
+}
+
+extern "C" int fbp_marginals(const fbp_graph *gc, float *out_p1, int out_is_device)
+{
+    t_err.clear();
+    fbp_graph *g = const_cast<fbp_graph *>(gc);
+    if (!g || (!out_p1 && g->h.nv > 0)) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    if (g->h.nv == 0) return FBP_OK;
+    float *dst = out_p1;
+    if (!out_is_device) {
+        if (!g->p1 && dalloc_n(g, &g->p1, (size_t)g->h.nv)) return FBP_ERR_OOM;
+        dst = g->p1;
+    }
+    launch_marginals(g->d, g->a2v[g->cur], dst, g->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (!out_is_device) {
+        CUDA_TRY(cudaMemcpyAsync(out_p1, g->p1, sizeof(float) * g->h.nv, cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+    return FBP_OK;
+}
+
+extern "C" int fbp_set_evidence(fbp_graph *g, int32_t var, int8_t value)
+{
+    t_err.clear();
+    if (!g || var < 0 || var >= g->h.nv || value < -1 || value > 1)
+        return fail(FBP_ERR_INVALID_ARG, "bad argument");
+    g->evidence[var] = value;
+    g->phi[var] = phi_of(g->prior[var], value);
+    CUDA_TRY(cudaMemcpyAsync(const_cast<float *>(g->d.phi) + var, &g->phi[var], sizeof(float),
+                             cudaMemcpyHostToDevice, g->stream));
+    return FBP_OK;
+}
+
+extern "C" int fbp_messages_export(const fbp_graph *gc, float *a2v)
+{
+    t_err.clear();
+    fbp_graph *g = const_cast<fbp_graph *>(gc);
+    if (!g || (!a2v && g->h.ne)) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->h.ne) return FBP_OK;
+    if (!g->pairs && dalloc_n(g, &g->pairs, 2 * (size_t)g->h.ne)) return FBP_ERR_OOM;
+    launch_decode_pairs(g->a2v[g->cur], g->pairs, g->h.ne, g->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(a2v, g->pairs, sizeof(float) * 2 * g->h.ne, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return FBP_OK;
+}
+
+extern "C" int fbp_messages_import(fbp_graph *g, const float *a2v)
+{
+    t_err.clear();
+    if (!g || (!a2v && g->h.ne)) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->h.ne) return FBP_OK;
+    for (int64_t i = 0; i < 2 * (int64_t)g->h.ne; ++i)
+        if (!(a2v[i] >= 0.f) || !std::isfinite(a2v[i])) return fail(FBP_ERR_INVALID_ARG, "message %lld invalid", (long long)i / 2);
+    if (!g->pairs && dalloc_n(g, &g->pairs, 2 * (size_t)g->h.ne)) return FBP_ERR_OOM;
+    CUDA_TRY(cudaMemcpyAsync(g->pairs, a2v, sizeof(float) * 2 * g->h.ne, cudaMemcpyHostToDevice, g->stream));
+    launch_encode_pairs(g->pairs, g->a2v[g->cur], g->h.ne, g->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return FBP_OK;
+}
+
+extern "C" int fbp_messages_reset(fbp_graph *g)
+{
+    t_err.clear();
+    if (!g) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    launch_fill(g->a2v[g->cur], 1.0f, g->h.ne, g->stream);
+    CUDA_TRY(cudaGetLastError());
+    return FBP_OK;
+}
+
+extern "C" int fbp_get_stats(const fbp_graph *g, fbp_stats *out)
+{
+    if (!g || !out) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    *out = g->stats;
+    return FBP_OK;
+}

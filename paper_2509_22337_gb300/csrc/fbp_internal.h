@@ -1,0 +1,66 @@
+// Internal interface between the host side (fbp_host.cpp) and the CUDA
+// kernels (fbp_kernels.cu) of the belief-propagation library.
+//
+// Message encoding.  A binary message (m0, m1) is stored as one float rho:
+//   rho >= +0  means (m0, m1) proportional to (rho, 1)   [m1 is the larger]
+//   rho <= -0  means (m0, m1) proportional to (1, -rho)  [m0 is the larger]
+// so |rho| in [0, 1] is the smaller entry over the larger one and the sign bit
+// says which entry is the larger.  +0 is the hard message (0, 1), -0 the hard
+// message (1, 0), +-1 the uniform message.  This keeps the full FP32 relative
+// precision of both normalised entries in 4 bytes instead of 8, and decoding
+// is a select, not a transcendental.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fbp {
+
+constexpr int kTypeAND = 0, kTypeOR = 1, kTypeNOT = 2, kTypeEQ = 3, kTypeNOISY_IMPLY = 4,
+              kTypeNOISY_AND = 5, kTypePRIOR = 6;
+
+// Number of residual slots one iteration spreads its atomics over.
+constexpr int kResSlots = 64;
+
+struct DevGraph {
+    int32_t nv = 0, na = 0, ne = 0;
+    const int32_t *fptr = nullptr;    // [na+1] factor-major row offsets
+    const uint8_t *ftype = nullptr;   // [na]
+    const float *fparam = nullptr;    // [na]
+    const int32_t *fvars = nullptr;   // [ne] variable of each edge
+    const int32_t *efac = nullptr;    // [ne] factor of each edge
+    const int32_t *vptr = nullptr;    // [nv+1] variable-major row offsets
+    const int32_t *vedge = nullptr;   // [ne] edge ids of each variable, ascending
+    const float *phi = nullptr;       // [nv] unary potential, rho-encoded
+};
+
+struct IterCtl {
+    unsigned *res = nullptr;           // [kResSlots] residual bits of this iteration
+    unsigned long long *guards = nullptr;
+};
+
+int num_sms();
+
+// Flooding (PARALL) iteration: phase 1 (Eq. 1) over every variable, then
+// phase 2 (closed-form local structure) over every factor.
+void launch_v2a_flood(const DevGraph &g, const float *a2v, float *v2a, cudaStream_t s);
+void launch_a2v_flood(const DevGraph &g, const float *v2a, float *a2v, IterCtl ctl,
+                      cudaStream_t s);
+// One level of a static schedule (Sec. 4.3.1), one thread per message: every
+// v*->a message the edge needs is formed from the level-start snapshot (an
+// edge updated in an earlier level of this half-iteration is read from nxt,
+// any other from cur), then the closed-form a->v message goes to nxt.
+// dres (optional) receives |delta m1| of every written edge.
+void launch_level(const DevGraph &g, const int32_t *lev_edges, int32_t n, int32_t level,
+                  const int32_t *vlev, const float *cur, float *nxt, IterCtl ctl, float *dres,
+                  cudaStream_t s);
+// Eq. (3).
+void launch_marginals(const DevGraph &g, const float *a2v, float *p1, cudaStream_t s);
+// rho <-> normalised (m0, m1) pairs.
+void launch_decode_pairs(const float *rho, float *pairs, int32_t n, cudaStream_t s);
+void launch_encode_pairs(const float *pairs, float *rho, int32_t n, cudaStream_t s);
+void launch_fill(float *x, float v, int32_t n, cudaStream_t s);
+void launch_copy_edges(const int32_t *edges, int32_t n, const float *src, float *dst,
+                       cudaStream_t s);
+
+}  // namespace fbp

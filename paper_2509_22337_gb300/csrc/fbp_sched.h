@@ -1,0 +1,49 @@
+// Host-side graph layout and scheduling: the factor-major CSR and its
+// variable-major transpose (Sec. 4.3.2), update strategy -> integer ranks
+// (Table 1, Definition 2), and the dependency analysis of Algorithm 2.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "fbp.h"
+
+namespace fbp {
+
+struct HostCSR {
+    int32_t nv = 0, na = 0, ne = 0;
+    std::vector<int64_t> fptr;    // [na+1]
+    std::vector<int32_t> fvars;   // [ne]
+    std::vector<uint8_t> ftype;   // [na]
+    std::vector<float> fparam;    // [na]
+    std::vector<int32_t> efac;    // [ne] factor of each edge
+    std::vector<int32_t> vptr;    // [nv+1]
+    std::vector<int32_t> vedge;   // [ne] edges of each variable, ascending id
+};
+
+// Sets the thread-local error message; returns code.
+int fail(int code, const char *fmt, ...);
+
+void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
+                    const uint8_t *ftype, const float *fparam, HostCSR &h);
+
+// Per-edge rank of a static strategy (PARALL, SEQFIX, TOPO, TOPO_FB, CUSTOM_RANK);
+// half = 1 selects the backward half of TOPO_FB.
+int build_ranks(const HostCSR &h, const fbp_schedule_spec &spec, int half, std::vector<int64_t> &rank);
+
+// Algorithm 2 over `edges` (all edges when NULL): canonical (rank, edge id)
+// order, greedy cuts.  lp = level_ptr, le = level_edges.
+void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edges, int64_t n,
+                       std::vector<int64_t> &lp, std::vector<int32_t> &le);
+
+// The residual strategy's classes for the next iteration from the previous
+// iteration's per-edge |delta m1|; fills rank for every edge and the active
+// edge list; returns the number of active edges.
+int64_t residual_classes(const HostCSR &h, const float *dres, double tol, int64_t *rank,
+                         std::vector<int32_t> &act);
+
+}  // namespace fbp
+
+struct fbp_graph;
+int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                     double *residual_out);

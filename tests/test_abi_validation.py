@@ -1,0 +1,41 @@
+"""Argument validation of fbp_graph_create runs before any device call, so
+these error paths are checked on the CPU."""
+import numpy as np
+import pytest
+
+from paper_2509_22337_gb300 import build as B
+from paper_2509_22337_gb300 import fbp as F
+from paper_2509_22337_gb300 import gen
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return F.load()
+
+
+def _create(g, **kw):
+    args = dict(n_vars=g.n_vars, n_factors=g.n_factors, factor_ptr=g.factor_ptr,
+                factor_vars=g.factor_vars, factor_type=g.factor_type, factor_param=g.factor_param,
+                prior_p1=g.prior_p1, evidence=g.evidence, alloc=None, stream=0)
+    args.update(kw)
+    return F.fbp_graph_create(**args)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda g: dict(factor_vars=np.where(np.arange(g.n_edges) == 3, 99, g.factor_vars)), "out of range"),
+    (lambda g: dict(factor_vars=np.where(np.arange(g.n_edges) == 3, 0, g.factor_vars)), "twice"),
+    (lambda g: dict(factor_type=np.array([6, 6, 4, 0, 9], np.uint8)), "unknown type"),
+    (lambda g: dict(factor_type=np.array([6, 2, 4, 0, 1], np.uint8)), "arity"),
+    (lambda g: dict(factor_param=np.array([1.5, 0.6, 0.9, 0, 0], np.float32)), "outside"),
+    (lambda g: dict(factor_ptr=np.array([0, 1, 2, 1, 7, 10], np.int64)), "decreases"),
+    (lambda g: dict(prior_p1=np.array([2, 0, 0, 0, 0], np.float32)), "prior"),
+    (lambda g: dict(evidence=np.array([3, 0, 0, 0, 0], np.int8)), "evidence"),
+    (lambda g: dict(n_vars=-1), "negative"),
+])
+def test_invalid_graph_rejected(lib, mutate, msg):
+    g = gen.fig1_example()
+    with pytest.raises(F.FbpError) as ei:
+        _create(g, **mutate(g))
+    assert ei.value.code == F.FBP_ERR_INVALID_ARG
+    assert msg in str(ei.value)

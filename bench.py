@@ -110,14 +110,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_sweep(g):
-    """Bytes one full pass over every edge must move in the level kernel (see
-    the roofline section of the design notes): per edge the level entry and the
-    old and new message (12 B), per incidence read while forming v->a messages
-    the edge id, its level and its message (12 B), and per factor/variable
-    row headers and unary potentials."""
+def algorithmic_bytes_per_half(g):
+    """Bytes one half-iteration (one pass over every level of one level list)
+    of the persistent level engine must move at minimum: per edge the old and
+    the new message (8 B), its row record (16 B) and its var-major
+    (edge, level) pair (8 B); per factor one work item (16 B); per variable
+    its unary potential (4 B).  Messages gathered while forming v->a products
+    are re-reads of the same 4 B/edge array and are not counted again."""
     E, V, A = g.n_edges, g.n_vars, g.n_factors
-    return 12 * E + 12 * E + 12 * V + 13 * A
+    return 32 * E + 16 * A + 4 * V
+
+
+def algorithmic_bytes_flood(g):
+    """Bytes one flooding iteration must move: phase 1 reads each edge's id in
+    its variable's row (4 B), gathers the a->v message (4 B) and scatters the
+    v->a message (4 B); phase 2 reads the v->a message (4 B) and the old a->v
+    message (4 B) and writes the new one (4 B); plus row offsets and unary
+    potentials (8 B/variable) and row offset, type and parameter (9 B/factor)."""
+    E, V, A = g.n_edges, g.n_vars, g.n_factors
+    return 24 * E + 8 * V + 9 * A
 
 
 def run_gpu(args):
@@ -188,21 +199,29 @@ def run_gpu(args):
         tot_updates = u.item()
     value = tot_updates / (t_max / 1e3)
 
-    # roofline of the dominant kernel: one level launch per level per half
+    # roofline of the dominant kernel
     sweeps = st["iters"]
-    level_launches = st["kernel_launches"]
+    launches_per_step = max(st["kernel_launches"], 1)
     kernel_ms = float(np.median(run_ms))
-    per_launch_ms = kernel_ms / max(level_launches, 1)
-    bytes_per_launch = algorithmic_bytes_per_sweep(g) * 2 * sweeps / max(level_launches, 1)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    per_launch_ms = kernel_ms / launches_per_step
+    if strategy == "PARALL":
+        kname = "k_v2a_flood + k_a2v_flood"
+        bytes_per_launch = algorithmic_bytes_flood(g) * sweeps / launches_per_step
+    else:
+        kname = "k_engine (persistent level engine, one launch per run)"
+        halves = 2 if strategy == "TOPO_FB" else 1
+        bytes_per_launch = algorithmic_bytes_per_half(g) * halves * sweeps / launches_per_step
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": "k_level_edges", "per_launch_us": round(per_launch_ms * 1e3, 3),
-            "bytes_per_launch": int(bytes_per_launch), "peak_source": "measured" if os.path.exists(
-                os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"}
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": kname,
+            "per_launch_us": round(per_launch_ms * 1e3, 3), "bytes_per_launch": int(bytes_per_launch),
+            "peak_source": "measured" if os.path.exists(peaks_path) else "fallback"}
+    levels_per_step = st["levels"] * sweeps
+    level_stats = {"levels_per_sweep": st["levels"],
+                   "us_per_level": round(kernel_ms * 1e3 / max(levels_per_step, 1), 3)}
 
     # end to end through the C ABI from host buffers
     e2e = None
@@ -245,7 +264,8 @@ def run_gpu(args):
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas{world}"},
             "time_to_converge_ms": round(total_ms / args.steps, 4),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "level_latency": level_stats, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
         print(json.dumps(line))

@@ -177,6 +177,21 @@ int fbp_messages_reset(fbp_graph *g);
 /* Counters of the last run. */
 int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
 
+/* Tuning and failure-detection options of a graph handle.
+ * FBP_OPT_SPIN_LIMIT   cycles a device-side barrier may wait before the run
+ *                      fails with FBP_ERR_TIMEOUT (default 4e9, about 2 s);
+ *                      0 makes every wait expire at once (used to test the
+ *                      timeout path).
+ * FBP_OPT_ENGINE_GRID  blocks of the persistent level engine in grid mode
+ *                      (0 = automatic choice of mode and size).
+ * FBP_OPT_ENGINE       1 (default): static strategies run in the persistent
+ *                      engine; 0: one launch per level (reference path).
+ * FBP_OPT_ENGINE_CLUSTER 0 (default): automatic; 1: never run the engine as
+ *                      one thread-block cluster; 8 or 16: always, with that
+ *                      cluster size. */
+enum { FBP_OPT_SPIN_LIMIT = 1, FBP_OPT_ENGINE_GRID = 2, FBP_OPT_ENGINE = 3, FBP_OPT_ENGINE_CLUSTER = 4 };
+int fbp_set_option(fbp_graph *g, int32_t option, int64_t value);
+
 /* Free the graph's device memory (after the stream's pending work). */
 void fbp_graph_destroy(fbp_graph *g);
 

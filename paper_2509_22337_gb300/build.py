@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfbp.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fbp_kernels.cu", "fbp_host.cpp", "fbp_sched.cpp", "fbp_batch.cpp", "fbp_serve.cpp"]
+SOURCES = ["fbp_kernels.cu", "fbp_engine.cu", "fbp_host.cpp", "fbp_sched.cpp", "fbp_batch.cpp", "fbp_serve.cpp"]
 
 
 def nvcc() -> str:
@@ -36,7 +36,7 @@ def _flags(extra: list[str] | None = None) -> list[str]:
 def _compile(src: str, extra: list[str] | None) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "fbp.h"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj

@@ -1,0 +1,399 @@
+// Persistent level engine (sm_103a): a whole BP run of a static update
+// strategy in one launch.
+//
+// The dependency analysis (Algorithm 2) turns the strategy into ordered
+// levels; Sec. 4.3.1 executes each level in two phases (all needed
+// variable-to-factor messages from the level-start state, then the level's
+// factor-to-variable messages) with kernel launches per level.  Here every
+// level is one step of a persistent grid, separated from the next by a
+// barrier, and the convergence test runs on the device: a run of hundreds of
+// levels times tens of iterations is one launch and one host synchronisation.
+//
+// Lane plan.  The host packs each level into warp-sized groups of lanes: one
+// lane per variable of every factor the level touches, each factor whole
+// inside one warp.  The lane of a factor's position j forms the incoming v->a
+// message of position j (Eq. 1) by walking the variable's row; an a->v message
+// updated in an earlier level of this half-iteration is read from `nxt`, any
+// other from `cur` (the level-start snapshot).  The products meet in shared
+// memory; then every lane whose edge belongs to the level computes its closed
+// form a->v message (Eq. 4, fbp_msg.cuh).  All of a level's messages are
+// computed in one pass of one lane each.
+//
+// Level step.  Everything a lane needs except message values (its lane
+// record, its variable's row range and unary potential, the first kPre row
+// entries and which buffer each comes from) is read-only, so it is fetched for
+// the next level between the barrier's arrive and its wait.  After the wait a
+// level costs one round of message loads, the arithmetic and the stores.
+//  Cluster mode: the grid is one thread-block cluster and the barrier is the
+//  hardware cluster barrier (release/acquire).  It cannot time out: all
+//  blocks of a cluster are co-scheduled and run the same barrier sequence.
+//  Grid mode (cooperative launch, for levels wider than a cluster): a counter
+//  that only grows; one release-add per block; the block's first thread polls
+//  with acquire loads, bounded by spin_limit cycles, then raises the error
+//  word and every block leaves at its next barrier.
+// Message buffers change between levels, so they are read and written at L2
+// (ld/st.global.cg); the plan and the graph structure are read-only.
+#include "fbp_msg.cuh"
+
+namespace fbp {
+
+namespace {
+
+constexpr int kBlock = 256;    // threads per block
+constexpr int kMaxFan = 32;    // largest factor held by one warp (larger: per-edge path)
+constexpr int kPre = 8;        // row entries of a lane prefetched into registers
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void grid_arrive(unsigned *counter)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add(counter, 1u);
+}
+
+// Returns nonzero on timeout or when another block reported an error.
+__device__ __forceinline__ int grid_wait(const unsigned *counter, unsigned target, int *err, long long spin_limit)
+{
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        const long long t0 = clock64();
+        int polls = 0;
+        while ((int)(ld_acquire(counter) - target) < 0) {
+            if (*(volatile int *)err) { fail = 1; break; }
+            if (clock64() - t0 > spin_limit) {
+                atomicExch(err, 1);
+                fail = 1;
+                break;
+            }
+            if (++polls > 64) __nanosleep(20);
+        }
+        if (*(volatile int *)err) fail = 1;
+        s_fail = fail;
+    }
+    __syncthreads();
+    return s_fail;
+}
+
+// Incoming v->a message of edge q = (a, v) at level L without prefetch (the
+// per-edge path of factors wider than a warp).
+__device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P, int q, int L,
+                                     const float *cur, const float *nxt)
+{
+    const int4 er = __ldg(A.erow + q);
+    P2 m = dec(__ldg(A.g.phi + er.z));
+    for (int k0 = er.x; k0 < er.y; k0 += kPre) {
+        float rr[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            rr[u] = 1.f;
+            if (k0 + u < er.y) {
+                const int2 ev = __ldg(P.vel + k0 + u);
+                if (ev.x != q) rr[u] = ev.y < L ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            m = mul(m, dec(rr[u]));
+            if (u & 1) resc(m);
+        }
+    }
+    return norm_max(m);
+}
+
+// A lane's read-only state for one level.
+struct Pre {
+    int4 rec;          // lane record: {edge q or -1, first | n<<5 | type<<11 | target<<14, p bits, variable}
+    float phi;
+    int e[kPre];       // first row entries (edge ids)
+    unsigned use_nxt;  // bit u: entry u was written earlier in this half-iteration
+    unsigned live;     // bit u: entry u exists and is not q itself
+    int kmore, kend;   // rest of the row
+};
+
+__device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
+                                         int s1)
+{
+    s.rec = make_int4(-1, 0, 0, 0);
+    s.use_nxt = 0u;
+    s.live = 0u;
+    s.kmore = s.kend = 0;
+    s.phi = 1.f;
+    if (slot >= s1) return;
+    s.rec = __ldg(P.lanes + slot);
+    const int2 er = __ldg(P.lrow + slot);  // independent of rec: both loads in flight together
+    const int q = s.rec.x;
+    if (q < 0) return;
+    s.phi = __ldg(A.g.phi + s.rec.w);
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        const int k = er.x + u;
+        s.e[u] = 0;
+        if (k < er.y) {
+            const int2 ev = __ldg(P.vel + k);
+            s.e[u] = ev.x;
+            if (ev.x != q) s.live |= 1u << u;
+            if (ev.y < La) s.use_nxt |= 1u << u;
+        }
+    }
+    s.kmore = er.x + kPre;
+    s.kend = er.y;
+}
+
+// One lane's share of a level: its position's v->a product, then (if its edge
+// is in the level) its factor's closed form a->v message.  Called by whole
+// warps (the __syncwarp()s).
+__device__ __forceinline__ void run_lane(const Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La,
+                                         const float *cur, float *nxt, P2 *sm, float &rmax,
+                                         unsigned long long &ng)
+{
+    const int q = s.rec.x;
+    const int pk = s.rec.y;
+    const bool tgt = q >= 0 && ((pk >> 14) & 1);
+    const float old = tgt ? __ldcg(cur + q) : 1.f;
+    P2 m{1.f, 1.f};
+    if (q >= 0) {
+        float r[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u)
+            r[u] = ((s.live >> u) & 1u) ? (((s.use_nxt >> u) & 1u) ? __ldcg(nxt + s.e[u]) : __ldcg(cur + s.e[u]))
+                                         : 1.f;
+        m = dec(s.phi);
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            m = mul(m, dec(r[u]));
+            if (u & 1) resc(m);
+        }
+        // the rest of a long row, kPre entries per step (entry loads first)
+        for (int k0 = s.kmore; k0 < s.kend; k0 += kPre) {
+            float rr[kPre];
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                rr[u] = 1.f;
+                if (k0 + u < s.kend) {
+                    const int2 ev = __ldg(P.vel + k0 + u);
+                    if (ev.x != q) rr[u] = ev.y < La ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                m = mul(m, dec(rr[u]));
+                if (u & 1) resc(m);
+            }
+        }
+        m = norm_max(m);
+    }
+    const int lane = threadIdx.x & 31;
+    sm[lane] = m;
+    __syncwarp();
+    if (tgt) {
+        const int first = pk & 31, n = (pk >> 5) & 63, type = (pk >> 11) & 7;
+        const float p = __int_as_float(s.rec.z);
+        const P2 mu = a2v_unified(type, p, n, lane - first, [&](int j) { return sm[first + j]; });
+        bool gd = false;
+        const float r = enc_fast(mu, gd);
+        ng += gd;
+        const float d = delta_p1_fast(r, old);
+        rmax = fmaxf(rmax, d);
+        __stcg(nxt + q, r);
+        if (A.dres) A.dres[q] = d;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ LevelPlanDev plan_at(const EngineArgs &A, int h)
+{
+    return h == 0 ? A.half[0] : A.half[1];
+}
+
+template <bool kCluster>
+__global__ void __launch_bounds__(kBlock, 1) k_engine(EngineArgs A)
+{
+    __shared__ P2 s_m[kBlock];
+    P2 *sm = s_m + (threadIdx.x & ~31);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    // A level's warp groups are dealt to warps round-robin over the blocks, so
+    // that a narrow level is spread over every SM of the grid instead of
+    // filling the first blocks: warp w of block b is global warp w*grid + b.
+    const int lane = threadIdx.x & 31;
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int nw = nthr >> 5;
+    const int my0 = gw * 32 + lane;  // this thread's slot offset in its first pass
+    float *cur = A.buf[0], *nxt = A.buf[1];
+    unsigned long long ng = 0;
+    unsigned target = 0;
+    int it, status = 1, failed = 0;
+    const bool empty = A.n_halves == 0 ||
+                       (A.half[0].n_levels == 0 && (A.n_halves < 2 || A.half[1].n_levels == 0));
+    Pre pre;
+    if (!empty) {
+        int h0 = 0;
+        while (plan_at(A, h0).n_levels == 0) ++h0;
+        const LevelPlanDev P0 = plan_at(A, h0);
+        prefetch(pre, A, P0, P0.level_base, __ldg(P0.lane_ptr) + my0, __ldg(P0.lane_ptr + 1));
+    }
+    for (it = 1; it <= A.max_iters && !failed && !empty; ++it) {
+        float rmax = 0.f;
+        for (int h = 0; h < A.n_halves && !failed; ++h) {
+            const LevelPlanDev P = plan_at(A, h);
+            for (int L = 0; L < P.n_levels; ++L) {
+                const int La = L + P.level_base;
+                const int s0 = __ldg(P.lane_ptr + L), s1 = __ldg(P.lane_ptr + L + 1);
+                run_lane(pre, A, P, La, cur, nxt, sm, rmax, ng);
+                for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
+                    Pre more;
+                    prefetch(more, A, P, La, slot, s1);
+                    run_lane(more, A, P, La, cur, nxt, sm, rmax, ng);
+                }
+                // factors wider than a warp: one thread per edge
+                const int b0 = __ldg(P.big_ptr + L), b1 = __ldg(P.big_ptr + L + 1);
+                for (int b = b0 + tid; b < b1; b += nthr) {
+                    const int e = __ldg(P.big + b);
+                    const int a = __ldg(A.g.efac + e);
+                    const int lo = __ldg(A.g.fptr + a), n = __ldg(A.g.fptr + a + 1) - lo;
+                    const P2 mu = a2v_unified(__ldg(A.g.ftype + a), __ldg(A.g.fparam + a), n, e - lo,
+                                              [&](int j) { return v2a_at(A, P, lo + j, La, cur, nxt); });
+                    bool gd = false;
+                    const float r = enc_fast(mu, gd);
+                    ng += gd;
+                    const float d = delta_p1_fast(r, __ldcg(cur + e));
+                    rmax = fmaxf(rmax, d);
+                    __stcg(nxt + e, r);
+                    if (A.dres) A.dres[e] = d;
+                }
+                if (L + 1 == P.n_levels && h + 1 == A.n_halves) {
+                    const float bm = block_max(rmax);
+                    if (threadIdx.x == 0 && bm > 0.f) atomicMax(A.res + (it - 1), __float_as_uint(bm));
+                }
+                if (kCluster) {
+                    cluster_arrive();
+                } else {
+                    grid_arrive(A.bar);
+                    target += gridDim.x;
+                }
+                {   // the next level (next half, or the next iteration's first level)
+                    int Ln = L + 1, hn = h;
+                    LevelPlanDev Pn = P;
+                    while (Ln >= Pn.n_levels) {
+                        Ln = 0;
+                        hn = hn + 1 < A.n_halves ? hn + 1 : 0;
+                        Pn = plan_at(A, hn);
+                        if (Pn.n_levels > 0) break;
+                    }
+                    prefetch(pre, A, Pn, Ln + Pn.level_base, __ldg(Pn.lane_ptr + Ln) + my0,
+                             __ldg(Pn.lane_ptr + Ln + 1));
+                }
+                if (kCluster) {
+                    cluster_wait();
+                } else if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
+                    failed = 1;
+                    break;
+                }
+            }
+            float *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        if (failed) break;
+        const float r = __uint_as_float(*(volatile unsigned *)(A.res + (it - 1)));
+        if (r < A.tol) {
+            status = 0;
+            break;
+        }
+    }
+    if (empty) {
+        status = 0;
+        it = 1;
+    }
+    if (ng) atomicAdd(A.guards, ng);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.out[0] = it > A.max_iters ? A.max_iters : it;
+        A.out[1] = failed ? -1 : status;
+    }
+}
+
+}  // namespace
+
+int engine_block() { return kBlock; }
+int engine_max_fan() { return kMaxFan; }
+
+int engine_max_grid()
+{
+    static int cap = 0;
+    if (!cap) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine<false>, kBlock, 0);
+        cap = per_sm * num_sms();
+        if (cap < 1) cap = 1;
+    }
+    return cap;
+}
+
+// Largest cluster (16 or 8 blocks, 0 if none) that can be scheduled for the
+// engine's block shape on this device.
+int engine_cluster_size()
+{
+    static int size = -1;
+    if (size < 0) {
+        size = 0;
+        cudaFuncSetAttribute(k_engine<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int c : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(c);
+            cfg.blockDim = dim3(kBlock);
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = c;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_engine<true>, &cfg) == cudaSuccess && n > 0) {
+                size = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+    }
+    return size;
+}
+
+cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream_t s)
+{
+    EngineArgs args = a;
+    if (cluster > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cluster);
+        cfg.blockDim = dim3(kBlock);
+        cfg.stream = s;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = cluster;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_engine<true>, args);
+    }
+    const int cap = engine_max_grid();
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    void *params[] = {&args};
+    return cudaLaunchCooperativeKernel((void *)k_engine<false>, dim3(grid), dim3(kBlock), params, 0, s);
+}
+
+}  // namespace fbp

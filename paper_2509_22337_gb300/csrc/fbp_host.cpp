@@ -65,10 +65,15 @@ float phi_of(float prior, int8_t ev)
 // graph handle
 // ---------------------------------------------------------------------------
 struct LevelSet {                    // one level list (one half of TOPO_FB)
-    std::vector<int64_t> lp;         // level_ptr
+    std::vector<int64_t> lp;         // level_ptr (Algorithm 2's S)
     std::vector<int32_t> le;         // level_edges (canonical order)
-    int32_t *d_le = nullptr;         // device copy of le
-    int32_t *d_vlev = nullptr;       // [E] var-major level index of each edge
+    // engine plan (device)
+    int4 *d_lanes = nullptr;
+    int2 *d_lrow = nullptr;
+    int32_t *d_lane_ptr = nullptr, *d_big = nullptr, *d_big_ptr = nullptr;
+    int2 *d_vel = nullptr;
+    int32_t max_lanes = 0;           // widest level, in lanes
+    int64_t n_lanes = 0;
 };
 
 struct fbp_graph {
@@ -93,6 +98,17 @@ struct fbp_graph {
     // residual strategy working state
     float *dres = nullptr;            // [E] |delta m1| of the last write
     int32_t *d_act = nullptr;         // [E] active edges (residual)
+    // persistent engine
+    int4 *erow = nullptr;             // [E] row record of each edge's variable
+    unsigned *d_res_it = nullptr;     // [res_cap] residual bits per iteration
+    int32_t res_cap = 0;
+    unsigned *d_bar = nullptr;        // [2] barrier words
+    int32_t *d_out = nullptr;         // [4] engine outputs
+    int32_t *h_out = nullptr;         // pinned copy
+    long long spin_limit = 4000000000LL;
+    int engine_grid = 0;              // 0 = automatic
+    int engine_cluster = 0;           // 0 = automatic, 1 = never, 8 or 16 = cluster size
+    int use_engine = 1;
     // per-iteration control
     unsigned *d_res = nullptr;
     unsigned long long *d_guards = nullptr;
@@ -147,27 +163,119 @@ void dfree(fbp_graph *g, void *p)
     else cudaFree(p);
 }
 
+void free_levels_one(fbp_graph *g, LevelSet &ls)
+{
+    dfree(g, ls.d_lanes);
+    dfree(g, ls.d_lrow);
+    ls.d_lrow = nullptr;
+    dfree(g, ls.d_lane_ptr);
+    dfree(g, ls.d_big);
+    dfree(g, ls.d_big_ptr);
+    dfree(g, ls.d_vel);
+    ls.d_lanes = nullptr;
+    ls.d_lane_ptr = ls.d_big = ls.d_big_ptr = nullptr;
+    ls.d_vel = nullptr;
+}
+
 void free_levels(fbp_graph *g)
 {
-    for (auto &ls : g->halves) {
-        dfree(g, ls.d_le);
-        dfree(g, ls.d_vlev);
-    }
+    for (auto &ls : g->halves) free_levels_one(g, ls);
     g->halves.clear();
 }
 
-// Upload one level list and the var-major level index of every edge.
+// Engine plan of one level list.  Per level, the factors the level touches
+// (in order of first appearance) are packed into warps of 32 lanes, one lane
+// per variable of the factor and every factor inside a single warp; each lane
+// record is {edge, first lane of its factor | n << 5 | type << 11 | in-level
+// bit << 14, p bits, variable}, with the variable's row range beside it in
+// lrow; idle lanes have edge -1.  Factors wider than a warp
+// go to a per-edge list.  vel[k] pairs the k-th var-major edge with its level
+// (INT_MAX if the edge is in no level: inactive under the residual strategy).
 int upload_levels(fbp_graph *g, LevelSet &ls)
 {
     const HostCSR &h = g->h;
+    const int32_t nl = (int32_t)ls.lp.size() - 1;
+    std::vector<int4> lanes;
+    std::vector<int2> lrow;
+    std::vector<int32_t> lane_ptr(1, 0), big, big_ptr(1, 0);
     std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max());
-    for (size_t L = 0; L + 1 < ls.lp.size(); ++L)
-        for (int64_t i = ls.lp[L]; i < ls.lp[L + 1]; ++i) elev[ls.le[i]] = (int32_t)L;
-    std::vector<int32_t> vlev(h.ne);
-    for (int32_t k = 0; k < h.ne; ++k) vlev[k] = elev[h.vedge[k]];
-    int rc = upload(g, &ls.d_le, ls.le.data(), ls.le.size());
-    if (!rc) rc = upload(g, &ls.d_vlev, vlev.data(), vlev.size());
+    std::vector<int64_t> stamp(h.na, -1);
+    std::vector<uint32_t> fmask(h.na, 0);
+    std::vector<int32_t> order;
+    const int maxfan = engine_max_fan();
+    int32_t max_lanes = 0;
+    for (int32_t L = 0; L < nl; ++L) {
+        order.clear();
+        for (int64_t i = ls.lp[L]; i < ls.lp[L + 1]; ++i) {
+            const int32_t e = ls.le[i];
+            elev[e] = L;
+            const int32_t a = h.efac[e];
+            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
+            if (n > maxfan) {
+                big.push_back(e);
+                continue;
+            }
+            if (stamp[a] != L) {
+                stamp[a] = L;
+                fmask[a] = 0;
+                order.push_back(a);
+            }
+            fmask[a] |= 1u << (e - lo);
+        }
+        const size_t base = lanes.size();
+        int used = 32;  // lanes used in the current warp
+        for (int32_t a : order) {
+            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
+            if (used + n > 32) {
+                while (lanes.size() % 32) {
+                    lanes.push_back(make_int4(-1, 0, 0, 0));
+                    lrow.push_back(make_int2(0, 0));
+                }
+                used = 0;
+            }
+            int32_t pb;
+            std::memcpy(&pb, &h.fparam[a], sizeof pb);
+            for (int32_t j = 0; j < n; ++j) {
+                const int32_t pk = used | (n << 5) | ((int32_t)h.ftype[a] << 11) |
+                                   ((int32_t)((fmask[a] >> j) & 1u) << 14);
+                const int32_t v = h.fvars[lo + j];
+                lanes.push_back(make_int4(lo + j, pk, pb, v));
+                lrow.push_back(make_int2(h.vptr[v], h.vptr[v + 1]));
+            }
+            used += n;
+        }
+        while (lanes.size() % 32) {
+            lanes.push_back(make_int4(-1, 0, 0, 0));
+            lrow.push_back(make_int2(0, 0));
+        }
+        max_lanes = std::max(max_lanes, (int32_t)(lanes.size() - base));
+        lane_ptr.push_back((int32_t)lanes.size());
+        big_ptr.push_back((int32_t)big.size());
+    }
+    std::vector<int2> vel(h.ne);
+    for (int32_t k = 0; k < h.ne; ++k) vel[k] = make_int2(h.vedge[k], elev[h.vedge[k]]);
+    free_levels_one(g, ls);
+    int rc = upload(g, &ls.d_lanes, lanes.data(), lanes.size());
+    if (!rc) rc = upload(g, &ls.d_lrow, lrow.data(), lrow.size());
+    if (!rc) rc = upload(g, &ls.d_lane_ptr, lane_ptr.data(), lane_ptr.size());
+    if (!rc) rc = upload(g, &ls.d_big, big.data(), big.size());
+    if (!rc) rc = upload(g, &ls.d_big_ptr, big_ptr.data(), big_ptr.size());
+    if (!rc) rc = upload(g, &ls.d_vel, vel.data(), vel.size());
+    ls.max_lanes = max_lanes;
+    ls.n_lanes = (int64_t)lanes.size();
     return rc;
+}
+
+// Row record of each edge's variable: {vptr[v], vptr[v+1], v, 0}.
+int upload_erow(fbp_graph *g)
+{
+    const HostCSR &h = g->h;
+    std::vector<int4> er(h.ne);
+    for (int32_t e = 0; e < h.ne; ++e) {
+        const int32_t v = h.fvars[e];
+        er[e] = make_int4(h.vptr[v], h.vptr[v + 1], v, 0);
+    }
+    return upload(g, &g->erow, er.data(), er.size());
 }
 
 int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
@@ -232,6 +340,7 @@ extern "C" void fbp_graph_destroy(fbp_graph *g)
     std::vector<void *> all = g->owned;
     for (void *p : all) dfree(g, p);
     if (g->h_res) cudaFreeHost(g->h_res);
+    if (g->h_out) cudaFreeHost(g->h_out);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
@@ -278,6 +387,9 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
         (rc = upload(g, &vptr, h.vptr.data(), h.vptr.size())) ||
         (rc = upload(g, &vedge, h.vedge.data(), h.vedge.size())) ||
         (rc = upload(g, &phi, g->phi.data(), g->phi.size())) ||
+        (rc = upload_erow(g)) ||
+        (rc = dalloc_n(g, &g->d_bar, 2)) ||
+        (rc = dalloc_n(g, &g->d_out, 4)) ||
         (rc = dalloc_n(g, &g->a2v[0], (size_t)h.ne)) ||
         (rc = dalloc_n(g, &g->d_res, (size_t)kResSlots)) ||
         (rc = dalloc_n(g, &g->d_guards, 1))) {
@@ -299,6 +411,7 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
     g->d.phi = phi;
     launch_fill(g->a2v[0], 1.0f, h.ne, g->stream);  // uniform initial messages
     cudaError_t e = cudaMallocHost((void **)&g->h_res, sizeof(unsigned) * kResSlots);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_out, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -436,62 +549,88 @@ int read_residual(fbp_graph *g, double *res)
     return FBP_OK;
 }
 
-// One half-iteration over a level list; messages go from a2v[cur] to the
-// other buffer, then the buffers swap.
-void run_half(fbp_graph *g, const LevelSet &ls, IterCtl ctl)
+int ensure_res_cap(fbp_graph *g, int32_t n)
 {
-    const float *cur = g->a2v[g->cur];
-    float *nxt = g->a2v[g->cur ^ 1];
-    for (size_t L = 0; L + 1 < ls.lp.size(); ++L) {
-        launch_level(g->d, ls.d_le + ls.lp[L], (int32_t)(ls.lp[L + 1] - ls.lp[L]), (int32_t)L, ls.d_vlev,
-                     cur, nxt, ctl, nullptr, g->stream);
-        g->stats.kernel_launches++;
-    }
-    g->cur ^= 1;
+    if (n <= g->res_cap) return FBP_OK;
+    dfree(g, g->d_res_it);
+    g->d_res_it = nullptr;
+    g->res_cap = 0;
+    int32_t cap = std::max<int32_t>(n, 64);
+    int rc = dalloc_n(g, &g->d_res_it, (size_t)cap);
+    if (rc) return rc;
+    g->res_cap = cap;
+    return FBP_OK;
 }
 
-}  // namespace
-
-extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
-                       double *residual_out)
+LevelPlanDev plan_of(const LevelSet &ls)
 {
-    t_err.clear();
-    if (!g || max_iters < 0 || !(tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
-    if (g->strategy == FBP_RESIDUAL) return fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
-    const HostCSR &h = g->h;
-    g->stats = fbp_stats{};
-    for (auto &ls : g->halves) g->stats.levels += (int32_t)ls.lp.size() - 1;
-    IterCtl ctl{g->d_res, g->d_guards};
-    CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
-    if (g->strategy == FBP_PARALL && !g->v2a) {
-        if (dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
+    LevelPlanDev p;
+    p.lanes = ls.d_lanes;
+    p.lrow = ls.d_lrow;
+    p.lane_ptr = ls.d_lane_ptr;
+    p.big = ls.d_big;
+    p.big_ptr = ls.d_big_ptr;
+    p.vel = ls.d_vel;
+    p.n_levels = (int32_t)ls.lp.size() - 1;
+    return p;
+}
+
+// Launch shape of the engine: one cluster (hardware barrier, the fastest
+// level step) when the widest level fits the cluster's prefetched work items,
+// otherwise a cooperative grid just wide enough for the widest level.
+// Launch shape of the engine.  Default: a cooperative grid of one block per
+// SM (a level's warps are spread round-robin over the blocks), grown if the
+// widest level needs more lanes.  Cluster mode (one cluster, hardware
+// barrier) only when asked for.
+void engine_shape(const fbp_graph *g, int *grid, int *cluster)
+{
+    int32_t mx = 32;
+    for (auto &ls : g->halves) mx = std::max(mx, ls.max_lanes);
+    const int lanes_per_block = engine_block();
+    *cluster = 0;
+    if (g->engine_grid > 0) {
+        *grid = g->engine_grid;
+        return;
     }
-    CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
-    int32_t it = 0;
-    double res = 0.0;
-    int status = FBP_NOT_CONVERGED;
-    for (it = 1; it <= max_iters; ++it) {
-        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
-        if (g->strategy == FBP_PARALL) {
-            launch_v2a_flood(g->d, g->a2v[g->cur], g->v2a, g->stream);
-            launch_a2v_flood(g->d, g->v2a, g->a2v[g->cur], ctl, g->stream);
-            g->stats.kernel_launches += 2;
-            g->stats.updates += h.ne;
-        } else {
-            for (auto &ls : g->halves) {
-                run_half(g, ls, ctl);
-                g->stats.updates += h.ne;
-            }
-        }
-        CUDA_TRY(cudaGetLastError());
-        int rc = read_residual(g, &res);
-        if (rc) return rc;
-        if (res < tol) {
-            status = FBP_OK;
-            break;
+    if (g->engine_cluster == 8 || g->engine_cluster == 16) {
+        const int csize = engine_cluster_size();
+        if (csize > 0) {
+            *cluster = std::min(g->engine_cluster, csize);
+            *grid = *cluster;
+            return;
         }
     }
-    if (it > max_iters) it = max_iters;
+    const int need = (mx + lanes_per_block - 1) / lanes_per_block;
+    *grid = std::min(std::max(need, num_sms()), engine_max_grid());
+}
+
+EngineArgs engine_args(fbp_graph *g)
+{
+    EngineArgs A;
+    A.g = g->d;
+    A.erow = g->erow;
+    A.n_halves = (int32_t)g->halves.size();
+    for (int h = 0; h < A.n_halves && h < 2; ++h) A.half[h] = plan_of(g->halves[h]);
+    A.buf[0] = g->a2v[g->cur];
+    A.buf[1] = g->a2v[g->cur ^ 1];
+    A.guards = g->d_guards;
+    A.bar = g->d_bar;
+    A.out = g->d_out;
+    A.spin_limit = g->spin_limit;
+    return A;
+}
+
+int engine_check(fbp_graph *g)
+{
+    CUDA_TRY(cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (g->h_out[2]) return fail(FBP_ERR_TIMEOUT, "a device-side barrier wait expired (spin limit %lld cycles)",
+                                 (long long)g->spin_limit);
+    return FBP_OK;
+}
+
+int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_out, double *residual_out)
+{
     CUDA_TRY(cudaEventRecord(g->ev1, g->stream));
     CUDA_TRY(cudaEventSynchronize(g->ev1));
     float ms = 0.f;
@@ -507,15 +646,138 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     return status;
 }
 
-// RESIDUAL strategy (dynamic levels rebuilt every iteration on the host).
+double residual_at(fbp_graph *g, int32_t it)
+{
+    if (it < 1) return 0.0;
+    unsigned bits = 0;
+    cudaMemcpy(&bits, g->d_res_it + (it - 1), sizeof bits, cudaMemcpyDeviceToHost);
+    float f;
+    std::memcpy(&f, &bits, sizeof f);
+    return (double)f;
+}
+
+// Static strategy, persistent engine: the whole run in one launch.
+int run_engine(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out, double *residual_out)
+{
+    const HostCSR &h = g->h;
+    int rc = ensure_res_cap(g, std::max(max_iters, 1));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(max_iters, 1), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, g->stream));
+    EngineArgs A = engine_args(g);
+    A.res = g->d_res_it;
+    A.max_iters = max_iters;
+    A.tol = (float)tol;
+    if (max_iters == 0) return finish_run(g, 0, 0.0, FBP_NOT_CONVERGED, iters_out, residual_out);
+    int grid = 1, cluster = 0;
+    engine_shape(g, &grid, &cluster);
+    CUDA_TRY(launch_engine(A, grid, cluster, g->stream));
+    g->stats.kernel_launches += 1;
+    rc = engine_check(g);
+    if (rc) return rc;
+    const int32_t it = g->h_out[0];
+    const int status = g->h_out[1] == 0 ? FBP_OK : FBP_NOT_CONVERGED;
+    g->cur ^= (it * A.n_halves) & 1;
+    g->stats.updates += (int64_t)it * A.n_halves * h.ne;
+    return finish_run(g, it, residual_at(g, it), status, iters_out, residual_out);
+}
+
+// Static strategy, one launch per level (the execution of Sec. 4.3.3).
+int run_per_level(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out, double *residual_out)
+{
+    const HostCSR &h = g->h;
+    int rc = ensure_res_cap(g, std::max(max_iters, 1));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(max_iters, 1), g->stream));
+    int grid = 1, cluster = 0;
+    engine_shape(g, &grid, &cluster);
+    int32_t it = 0;
+    double res = 0.0;
+    int status = FBP_NOT_CONVERGED;
+    for (it = 1; it <= max_iters; ++it) {
+        for (auto &ls : g->halves) {
+            LevelPlanDev full = plan_of(ls);
+            for (int32_t L = 0; L < full.n_levels; ++L) {
+                CUDA_TRY(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, g->stream));
+                EngineArgs A = engine_args(g);
+                LevelPlanDev one = full;
+                one.lane_ptr = full.lane_ptr + L;
+                one.big_ptr = full.big_ptr + L;
+                one.n_levels = 1;
+                one.level_base = L;
+                A.half[0] = one;
+                A.n_halves = 1;
+                A.res = g->d_res_it + (it - 1);
+                A.max_iters = 1;
+                A.tol = 0.f;
+                CUDA_TRY(launch_engine(A, grid, cluster, g->stream));
+                g->stats.kernel_launches += 1;
+            }
+            g->cur ^= 1;
+            g->stats.updates += h.ne;
+        }
+        rc = engine_check(g);
+        if (rc) return rc;
+        res = residual_at(g, it);
+        if (res < tol || h.ne == 0) {
+            status = FBP_OK;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    return finish_run(g, it, res, status, iters_out, residual_out);
+}
+
+}  // namespace
+
+extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                       double *residual_out)
+{
+    t_err.clear();
+    if (!g || max_iters < 0 || !(tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
+    const HostCSR &h = g->h;
+    g->stats = fbp_stats{};
+    for (auto &ls : g->halves) g->stats.levels += (int32_t)ls.lp.size() - 1;
+    CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
+    CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
+    if (g->strategy == FBP_RESIDUAL) return fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
+    if (g->strategy != FBP_PARALL)
+        return g->use_engine ? run_engine(g, max_iters, tol, iters_out, residual_out)
+                             : run_per_level(g, max_iters, tol, iters_out, residual_out);
+    IterCtl ctl{g->d_res, g->d_guards};
+    if (!g->v2a && dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
+    int32_t it = 0;
+    double res = 0.0;
+    int status = FBP_NOT_CONVERGED;
+    for (it = 1; it <= max_iters; ++it) {
+        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
+        launch_v2a_flood(g->d, g->a2v[g->cur], g->v2a, g->stream);
+        launch_a2v_flood(g->d, g->v2a, g->a2v[g->cur], ctl, g->stream);
+        g->stats.kernel_launches += 2;
+        g->stats.updates += h.ne;
+        CUDA_TRY(cudaGetLastError());
+        int rc = read_residual(g, &res);
+        if (rc) return rc;
+        if (res < tol) {
+            status = FBP_OK;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    return finish_run(g, it, res, status, iters_out, residual_out);
+}
+
+// RESIDUAL strategy: the classes of the next iteration come from the previous
+// iteration's per-edge changes, so its levels are rebuilt on the host every
+// iteration and each iteration is one engine launch.
 int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
                      double *residual_out)
 {
     const HostCSR &h = g->h;
-    g->stats = fbp_stats{};
-    IterCtl ctl{g->d_res, g->d_guards};
-    CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
-    CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
+    int rc = ensure_res_cap(g, std::max(max_iters, 1));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(max_iters, 1), g->stream));
     std::vector<float> dres(h.ne);
     std::vector<int64_t> rank(h.ne);
     std::vector<int32_t> act;
@@ -524,7 +786,6 @@ int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters
     int status = FBP_NOT_CONVERGED;
     LevelSet &ls = g->halves[0];
     for (it = 1; it <= max_iters; ++it) {
-        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
         int64_t n;
         if (it == 1) {
             std::fill(rank.begin(), rank.end(), 0);
@@ -538,49 +799,64 @@ int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters
             n = residual_classes(h, dres.data(), tol, rank.data(), act);
         }
         dependency_levels(h, rank.data(), act.data(), n, ls.lp, ls.le);
-        dfree(g, ls.d_le);
-        dfree(g, ls.d_vlev);
-        ls.d_le = nullptr;
-        ls.d_vlev = nullptr;
-        int rc = upload_levels(g, ls);
+        rc = upload_levels(g, ls);
         if (rc) return rc;
         g->stats.levels = (int32_t)ls.lp.size() - 1;
-        // inactive edges keep their value: start the next buffer as a copy
+        // inactive edges keep their value: start the other buffer as a copy
         CUDA_TRY(cudaMemcpyAsync(g->a2v[g->cur ^ 1], g->a2v[g->cur], sizeof(float) * h.ne,
                                  cudaMemcpyDeviceToDevice, g->stream));
         CUDA_TRY(cudaMemsetAsync(g->dres, 0, sizeof(float) * h.ne, g->stream));
-        const float *cur = g->a2v[g->cur];
-        float *nxt = g->a2v[g->cur ^ 1];
-        IterCtl c2 = ctl;
-        for (size_t L = 0; L + 1 < ls.lp.size(); ++L) {
-            launch_level(g->d, ls.d_le + ls.lp[L], (int32_t)(ls.lp[L + 1] - ls.lp[L]), (int32_t)L,
-                         ls.d_vlev, cur, nxt, c2, g->dres, g->stream);
-            g->stats.kernel_launches++;
+        CUDA_TRY(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, g->stream));
+        EngineArgs A = engine_args(g);
+        A.n_halves = 1;
+        A.res = g->d_res_it + (it - 1);
+        A.max_iters = 1;
+        A.tol = 0.f;
+        A.dres = g->dres;
+        if (n > 0) {
+            int grid = 1, cluster = 0;
+            engine_shape(g, &grid, &cluster);
+            CUDA_TRY(launch_engine(A, grid, cluster, g->stream));
+            g->stats.kernel_launches += 1;
         }
         g->cur ^= 1;
         g->stats.updates += n;
-        CUDA_TRY(cudaGetLastError());
-        rc = read_residual(g, &res);
+        rc = engine_check(g);
         if (rc) return rc;
-        if (res < tol) {
+        res = residual_at(g, it);
+        if (res < tol || n == 0) {
             status = FBP_OK;
             break;
         }
     }
     if (it > max_iters) it = max_iters;
-    CUDA_TRY(cudaEventRecord(g->ev1, g->stream));
-    CUDA_TRY(cudaEventSynchronize(g->ev1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
-    unsigned long long guards = 0;
-    CUDA_TRY(cudaMemcpy(&guards, g->d_guards, sizeof guards, cudaMemcpyDeviceToHost));
-    g->stats.iters = it;
-    g->stats.residual = res;
-    g->stats.run_ms = ms;
-    g->stats.guards = (int64_t)guards;
-    if (iters_out) *iters_out = it;
-    if (residual_out) *residual_out = res;
-    return status;
+    return finish_run(g, it, res, status, iters_out, residual_out);
+}
+
+extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
+{
+    t_err.clear();
+    if (!g) return fail(FBP_ERR_INVALID_ARG, "NULL graph");
+    switch (option) {
+    case FBP_OPT_SPIN_LIMIT:
+        if (value < 0) return fail(FBP_ERR_INVALID_ARG, "negative spin limit");
+        g->spin_limit = value;
+        return FBP_OK;
+    case FBP_OPT_ENGINE_GRID:
+        if (value < 0) return fail(FBP_ERR_INVALID_ARG, "negative grid");
+        g->engine_grid = (int)std::min<int64_t>(value, engine_max_grid());
+        return FBP_OK;
+    case FBP_OPT_ENGINE:
+        g->use_engine = value != 0;
+        return FBP_OK;
+    case FBP_OPT_ENGINE_CLUSTER:
+        if (value != 0 && value != 1 && value != 8 && value != 16)
+            return fail(FBP_ERR_INVALID_ARG, "cluster option must be 0, 1, 8 or 16");
+        g->engine_cluster = (int)value;
+        return FBP_OK;
+    default:
+        return fail(FBP_ERR_INVALID_ARG, "unknown option %d", option);
+    }
 }
 
 extern "C" int fbp_marginals(const fbp_graph *gc, float *out_p1, int out_is_device)

@@ -34,6 +34,42 @@ struct DevGraph {
     const float *phi = nullptr;       // [nv] unary potential, rho-encoded
 };
 
+// One half-iteration's levels, as the persistent engine reads them.
+struct LevelPlanDev {
+    const int4 *lanes = nullptr;       // warp-packed lane records, level after level
+    const int2 *lrow = nullptr;        // per lane: {row begin, row end} of the lane's variable
+    const int32_t *lane_ptr = nullptr; // [n_levels+1] (multiples of 32)
+    const int32_t *big = nullptr;      // edges of factors wider than a warp
+    const int32_t *big_ptr = nullptr;  // [n_levels+1]
+    const int2 *vel = nullptr;         // [ne] var-major (edge id, level of the edge)
+    int32_t n_levels = 0;
+    int32_t level_base = 0;            // index of lane_ptr[0]'s level (per-level launches)
+};
+
+struct EngineArgs {
+    DevGraph g;
+    const int4 *erow = nullptr;        // [ne] {row begin, row end, variable, 0} of each edge's variable
+    LevelPlanDev half[2];
+    int32_t n_halves = 1;
+    float *buf[2] = {nullptr, nullptr};// buf[0]: messages at launch; buf[1]: the other buffer
+    unsigned *res = nullptr;           // [max_iters] residual bits per iteration (zeroed)
+    unsigned long long *guards = nullptr;
+    float *dres = nullptr;             // optional [ne] |dP| of each written edge
+    unsigned *bar = nullptr;           // [2] barrier counter and generation (zeroed)
+    int32_t *out = nullptr;            // [4] iterations, status, error word, spare (zeroed)
+    int32_t max_iters = 0;
+    float tol = 0.f;
+    long long spin_limit = 0;          // clock64 cycles one barrier may wait
+};
+
+int engine_block();
+int engine_max_fan();
+int engine_max_grid();
+int engine_cluster_size();
+// cluster > 0: the grid is one cluster of that many blocks (hardware
+// barrier); otherwise a cooperative grid of `grid` blocks.
+cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream_t s);
+
 struct IterCtl {
     unsigned *res = nullptr;           // [kResSlots] residual bits of this iteration
     unsigned long long *guards = nullptr;
@@ -46,21 +82,11 @@ int num_sms();
 void launch_v2a_flood(const DevGraph &g, const float *a2v, float *v2a, cudaStream_t s);
 void launch_a2v_flood(const DevGraph &g, const float *v2a, float *a2v, IterCtl ctl,
                       cudaStream_t s);
-// One level of a static schedule (Sec. 4.3.1), one thread per message: every
-// v*->a message the edge needs is formed from the level-start snapshot (an
-// edge updated in an earlier level of this half-iteration is read from nxt,
-// any other from cur), then the closed-form a->v message goes to nxt.
-// dres (optional) receives |delta m1| of every written edge.
-void launch_level(const DevGraph &g, const int32_t *lev_edges, int32_t n, int32_t level,
-                  const int32_t *vlev, const float *cur, float *nxt, IterCtl ctl, float *dres,
-                  cudaStream_t s);
 // Eq. (3).
 void launch_marginals(const DevGraph &g, const float *a2v, float *p1, cudaStream_t s);
 // rho <-> normalised (m0, m1) pairs.
 void launch_decode_pairs(const float *rho, float *pairs, int32_t n, cudaStream_t s);
 void launch_encode_pairs(const float *pairs, float *rho, int32_t n, cudaStream_t s);
 void launch_fill(float *x, float v, int32_t n, cudaStream_t s);
-void launch_copy_edges(const int32_t *edges, int32_t n, const float *src, float *dst,
-                       cudaStream_t s);
 
 }  // namespace fbp

@@ -80,12 +80,14 @@ def load(path: str | None = None):
         L.fbp_messages_import.argtypes = [vp, vp]
         L.fbp_get_stats.argtypes = [vp, C.POINTER(fbp_stats)]
         L.fbp_messages_reset.argtypes = [vp]
+        L.fbp_set_option.argtypes = [vp, i32, i64]
         L.fbp_graph_destroy.argtypes = [vp]
         L.fbp_graph_destroy.restype = None
         L.fbp_last_error.restype = C.c_char_p
         for name in ("fbp_graph_create", "fbp_schedule_set", "fbp_run", "fbp_marginals",
                      "fbp_schedule_levels", "fbp_schedule_build_host", "fbp_set_evidence",
-                     "fbp_messages_export", "fbp_messages_import", "fbp_get_stats", "fbp_messages_reset"):
+                     "fbp_messages_export", "fbp_messages_import", "fbp_get_stats", "fbp_messages_reset",
+                     "fbp_set_option"):
             getattr(L, name).restype = C.c_int
         _bind_extras(L)
         _lib = L
@@ -251,6 +253,13 @@ def fbp_messages_import(g, a2v) -> int:
     return _check(load().fbp_messages_import(g, a.ctypes.data if a.size else None))
 
 
+FBP_OPT_SPIN_LIMIT, FBP_OPT_ENGINE_GRID, FBP_OPT_ENGINE, FBP_OPT_ENGINE_CLUSTER = 1, 2, 3, 4
+
+
+def fbp_set_option(g, option: int, value: int) -> int:
+    return _check(load().fbp_set_option(g, int(option), int(value)))
+
+
 def fbp_messages_reset(g) -> int:
     return _check(load().fbp_messages_reset(g))
 
@@ -291,6 +300,9 @@ class Graph:
 
     def set_messages(self, a2v):
         return fbp_messages_import(self.h, a2v)
+
+    def set_option(self, option, value):
+        return fbp_set_option(self.h, option, value)
 
     def reset(self):
         return fbp_messages_reset(self.h)

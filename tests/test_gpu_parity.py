@@ -247,3 +247,52 @@ def test_empty_and_degenerate_graphs(fbp):
     b = oracle_run(gc, "PARALL", 3, 0.0)
     assert_parity(a, b, "contradiction")
     assert a["stats"]["guards"] == b["guards"]
+
+
+def test_engine_equals_per_level_launches(fbp):
+    """The persistent engine and one launch per level (the paper's execution)
+    run the same arithmetic in the same order: bit-identical messages."""
+    for g, strat in [(gen.smartfl(n_layers=25, width=80, seed=61), "TOPO_FB"), (gen.tiny(), "SEQFIX")]:
+        G = fbp.Graph(g, strat)
+        G.run(6, 0.0)
+        a = G.messages()
+        G.close()
+        H = fbp.Graph(g, strat)
+        H.set_option(fbp.FBP_OPT_ENGINE, 0)
+        H.run(6, 0.0)
+        b = H.messages()
+        assert H.stats()["kernel_launches"] > 6
+        H.close()
+        assert np.array_equal(a, b), (g.name, strat)
+
+
+@pytest.mark.parametrize("grid", [1, 3, 17])
+def test_engine_grid_size_does_not_change_results(fbp, grid):
+    g = gen.smartfl(n_layers=15, width=60, seed=62)
+    ref = gpu_run(fbp, g, "TOPO_FB", 5, 0.0)
+    G = fbp.Graph(g, "TOPO_FB")
+    G.set_option(fbp.FBP_OPT_ENGINE_GRID, grid)
+    G.run(5, 0.0)
+    assert np.array_equal(G.messages().astype(np.float64), ref["a2v"])
+    G.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives(fbp):
+    """Failure detection without a GPU fault: a spin limit of 0 makes every
+    device-side barrier wait expire at once; the run must return
+    FBP_ERR_TIMEOUT and the context must stay usable."""
+    g = gen.smartfl(n_layers=10, width=40, seed=63)
+    G = fbp.Graph(g, "TOPO_FB")
+    G.set_option(fbp.FBP_OPT_ENGINE_GRID, 4)
+    G.set_option(fbp.FBP_OPT_SPIN_LIMIT, 0)
+    with pytest.raises(fbp.FbpError) as ei:
+        G.run(3, 0.0)
+    assert ei.value.code == fbp.FBP_ERR_TIMEOUT
+    G.set_option(fbp.FBP_OPT_SPIN_LIMIT, 4_000_000_000)
+    G.reset()
+    status, it, res = G.run(3, 0.0)
+    assert it == 3
+    p = G.marginals()
+    G.close()
+    ref = gpu_run(fbp, g, "TOPO_FB", 3, 0.0)
+    assert np.array_equal(p.astype(np.float64), ref["p"])

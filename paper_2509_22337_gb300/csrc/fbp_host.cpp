@@ -5,6 +5,7 @@
 // Launch" / "Message Passing").
 #include "fbp.h"
 #include "fbp_internal.h"
+#include "fbp_flood.h"
 #include "fbp_sched.h"
 
 #include <algorithm>
@@ -109,6 +110,10 @@ struct fbp_graph {
     int engine_grid = 0;              // 0 = automatic
     int engine_cluster = 0;           // 0 = automatic, 1 = never, 8 or 16 = cluster size
     int use_engine = 1;
+    // flooding plan
+    FloodPlanDev flood;
+    bool flood_ready = false;
+    int flood_staged = 0;
     // per-iteration control
     unsigned *d_res = nullptr;
     unsigned long long *d_guards = nullptr;
@@ -276,6 +281,64 @@ int upload_erow(fbp_graph *g)
         er[e] = make_int4(h.vptr[v], h.vptr[v + 1], v, 0);
     }
     return upload(g, &g->erow, er.data(), er.size());
+}
+
+// Flooding plan: variables by degree class (one thread / one warp per row,
+// or chunks of a hub row), and the shared-memory staging size of phase 2.
+int build_flood_plan(fbp_graph *g)
+{
+    const HostCSR &h = g->h;
+    FloodPlanDev F;
+    std::vector<int32_t> small, medium;
+    std::vector<int4> hub;
+    std::vector<int32_t> hub_n;
+    for (int32_t v = 0; v < h.nv; ++v) {
+        const int32_t lo = h.vptr[v], hi = h.vptr[v + 1], d = hi - lo;
+        if (d <= 2) continue;  // the lean kernel's rows
+        if (d <= kFloodSmallMax) {
+            small.push_back(v);
+            continue;
+        }
+        if (d <= kFloodMediumMax) {
+            medium.push_back(v);
+            continue;
+        }
+        const int32_t c0 = (int32_t)hub.size();
+        const int32_t nc = (d + kFloodHubChunk - 1) / kFloodHubChunk;
+        for (int32_t c = 0; c < nc; ++c) {
+            hub.push_back(make_int4(v, lo + c * kFloodHubChunk, std::min(hi, lo + (c + 1) * kFloodHubChunk), c0));
+            hub_n.push_back(nc);
+        }
+    }
+    F.n_small = (int32_t)small.size();
+    F.nb_small = (F.n_small + 255) / 256;
+    F.n_medium = (int32_t)medium.size();
+    F.nb_medium = (F.n_medium + 7) / 8;
+    F.n_hub = (int32_t)hub.size();
+    int32_t *d_small = nullptr, *d_medium = nullptr, *d_hub_n = nullptr;
+    int4 *d_hub = nullptr;
+    XP *d_agg = nullptr;
+    int rc = upload(g, &d_small, small.data(), small.size());
+    if (!rc) rc = upload(g, &d_medium, medium.data(), medium.size());
+    if (!rc) rc = upload(g, &d_hub, hub.data(), hub.size());
+    if (!rc) rc = upload(g, &d_hub_n, hub_n.data(), hub_n.size());
+    if (!rc) rc = dalloc_n(g, &d_agg, std::max<size_t>(hub.size(), 1));
+    if (rc) return rc;
+    F.small = d_small;
+    F.medium = d_medium;
+    F.hub = d_hub;
+    F.hub_nchunks = d_hub_n;
+    F.agg = d_agg;
+    int32_t mx = 0;
+    for (int32_t a0 = 0; a0 < h.na; a0 += 256) {
+        const int32_t a1 = std::min(a0 + 256, h.na);
+        mx = std::max(mx, (int32_t)(h.fptr[a1] - h.fptr[a0]));
+    }
+    g->flood_staged = std::min(mx, 4096);  // 28 B of shared memory per staged entry
+    flood_prepare(flood_smem_bytes(g->flood_staged));
+    g->flood = F;
+    g->flood_ready = true;
+    return FBP_OK;
 }
 
 int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
@@ -745,27 +808,39 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     if (g->strategy != FBP_PARALL)
         return g->use_engine ? run_engine(g, max_iters, tol, iters_out, residual_out)
                              : run_per_level(g, max_iters, tol, iters_out, residual_out);
+    // flooding: iterations are queued in growing batches; a device-side check
+    // marks the run done and later kernels of the batch return at once
     IterCtl ctl{g->d_res, g->d_guards};
     if (!g->v2a && dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
-    int32_t it = 0;
-    double res = 0.0;
-    int status = FBP_NOT_CONVERGED;
-    for (it = 1; it <= max_iters; ++it) {
-        CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
-        launch_v2a_flood(g->d, g->a2v[g->cur], g->v2a, g->stream);
-        launch_a2v_flood(g->d, g->v2a, g->a2v[g->cur], ctl, g->stream);
-        g->stats.kernel_launches += 2;
-        g->stats.updates += h.ne;
-        CUDA_TRY(cudaGetLastError());
-        int rc = read_residual(g, &res);
+    if (!g->flood_ready) {
+        int rc = build_flood_plan(g);
         if (rc) return rc;
-        if (res < tol) {
-            status = FBP_OK;
-            break;
-        }
     }
-    if (it > max_iters) it = max_iters;
-    return finish_run(g, it, res, status, iters_out, residual_out);
+    int rc = ensure_res_cap(g, std::max(max_iters, 1));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, g->stream));
+    const int launches_per_iter = (h.nv > 0) + (g->flood.n_hub > 0) +
+                                  (g->flood.nb_small + g->flood.nb_medium + g->flood.n_hub > 0) + (h.na > 0) + 1;
+    int32_t next = 1, batch = 4;
+    bool done = false;
+    while (next <= max_iters && !done) {
+        const int32_t last = std::min(max_iters, next + batch - 1);
+        for (int32_t it = next; it <= last; ++it) {
+            flood_iteration(g->d, g->flood, g->a2v[g->cur], g->v2a, ctl, g->flood_staged, it, (float)tol,
+                            g->d_res_it, g->d_out, g->stream);
+            g->stats.kernel_launches += launches_per_iter;
+        }
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        done = g->h_out[0] != 0;
+        next = last + 1;
+        batch = std::min(batch * 2, 64);
+    }
+    const int32_t it = max_iters == 0 ? 0 : g->h_out[1];
+    g->stats.updates += (int64_t)it * h.ne;
+    return finish_run(g, it, residual_at(g, it), done ? FBP_OK : FBP_NOT_CONVERGED, iters_out, residual_out);
 }
 
 // RESIDUAL strategy: the classes of the next iteration come from the previous

@@ -77,11 +77,6 @@ struct IterCtl {
 
 int num_sms();
 
-// Flooding (PARALL) iteration: phase 1 (Eq. 1) over every variable, then
-// phase 2 (closed-form local structure) over every factor.
-void launch_v2a_flood(const DevGraph &g, const float *a2v, float *v2a, cudaStream_t s);
-void launch_a2v_flood(const DevGraph &g, const float *v2a, float *a2v, IterCtl ctl,
-                      cudaStream_t s);
 // Eq. (3).
 void launch_marginals(const DevGraph &g, const float *a2v, float *p1, cudaStream_t s);
 // rho <-> normalised (m0, m1) pairs.

@@ -151,8 +151,17 @@ __device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM 
     return P2{fmaf(c0, Ps, fmaf(c1, P0, c2 * D0)), fmaf(d0, P1, fmaf(d1, D, d2 * Ps))};
 }
 
-// Encoding with a correctly rounded reciprocal instead of a division (result
-// within 1 ulp of the quotient, clamped to |rho| <= 1); zero mass -> uniform.
+// Hardware reciprocal approximation (rcp.approx.f32: relative error within a
+// couple of ulp, denormals kept).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Encoding through the reciprocal of the larger entry (result within a few
+// ulp of the quotient, clamped to |rho| <= 1); zero mass -> uniform.
 __device__ __forceinline__ float enc_fast(P2 m, bool &guard)
 {
     const float s = m.m0 + m.m1;
@@ -161,16 +170,16 @@ __device__ __forceinline__ float enc_fast(P2 m, bool &guard)
         return 1.f;
     }
     const float mx = fmaxf(m.m0, m.m1), mn = fminf(m.m0, m.m1);
-    const float r = fminf(mn * __frcp_rn(mx), 1.f);
+    const float r = fminf(mn * rcp_approx(mx), 1.f);
     return m.m1 >= m.m0 ? r : -r;
 }
 
-// delta_p1 for the convergence test only: fast divisions (a few ulp).
+// delta_p1 for the convergence test only: approximate reciprocals (a few ulp).
 __device__ __forceinline__ float delta_p1_fast(float rn, float ro)
 {
     const float an = fabsf(rn), ao = fabsf(ro);
-    if (signbit(rn) == signbit(ro)) return __fdividef(fabsf(ao - an), (1.f + an) * (1.f + ao));
-    return __fdividef(1.f - an, 2.f * (1.f + an)) + __fdividef(1.f - ao, 2.f * (1.f + ao));
+    if (signbit(rn) == signbit(ro)) return fabsf(ao - an) * rcp_approx((1.f + an) * (1.f + ao));
+    return (1.f - an) * rcp_approx(2.f * (1.f + an)) + (1.f - ao) * rcp_approx(2.f * (1.f + ao));
 }
 
 // Warp max of a non-negative float, then block max via shared memory; the

@@ -1,0 +1,472 @@
+// Batched form (include/fbp_batch.h): many independent graphs in one run.
+//
+// The graphs are split by the shape of their iteration: flooding (PARALL)
+// graphs form one union graph run by the flooding kernels; graphs with a
+// static strategy form one union graph per number of level lists per
+// iteration (one for SEQFIX/TOPO/CUSTOM_RANK, two for TOPO_FB), run by one
+// persistent level-engine launch.  Each member keeps the levels of its own
+// Algorithm 2 (a union-wide Algorithm 2 would cut levels where another graph
+// needs a cut, which changes a member's semantics); level k of every member
+// is merged into level k of the union.  Members carry their own tolerance and
+// iteration limit; the device marks each one done at its own stopping
+// iteration and freezes its messages, so every member ends exactly where a
+// single-graph run of it ends.  The parts run concurrently on separate streams.
+#include "fbp_batch.h"
+#include "fbp_graph_impl.h"
+
+#include <algorithm>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+using namespace fbp;
+
+namespace {
+
+enum { kFlood = 0, kStatic1 = 1, kStatic2 = 2, kParts = 3 };
+
+struct Part {
+    fbp_graph *g = nullptr;
+    std::vector<int32_t> members;          // batch indices
+    std::vector<int32_t> var_off, fac_off, edge_off;
+    int32_t max_iters = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device per-member state
+    int32_t *done = nullptr, *iters = nullptr, *active = nullptr;
+    unsigned *res = nullptr, *last_res = nullptr;
+    float *tol = nullptr;
+    int32_t *maxit = nullptr;
+    int32_t *vgraph = nullptr, *fgraph = nullptr;
+    BatchCtl ctl() const
+    {
+        BatchCtl c;
+        c.n_graphs = (int32_t)members.size();
+        c.done = done;
+        c.iters = iters;
+        c.res = res;
+        c.last_res = last_res;
+        c.tol = tol;
+        c.max_iters = maxit;
+        c.active = active;
+        return c;
+    }
+};
+
+int kind_of(int strategy)
+{
+    if (strategy == FBP_PARALL) return kFlood;
+    if (strategy == FBP_TOPO_FB) return kStatic2;
+    return kStatic1;
+}
+
+}  // namespace
+
+struct fbp_batch {
+    int32_t n = 0;
+    std::vector<int32_t> part_of, slot_of;  // per batch graph: part and member index
+    std::vector<int32_t> nv, ne;
+    Part parts[kParts];
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr};
+    fbp_batch_tuning tuning{0, 0};
+    fbp_stats stats{};
+    float *scratch = nullptr;  // [largest union] marginals / pairs staging
+    size_t scratch_n = 0;
+};
+
+namespace {
+
+int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_allocator *alloc)
+{
+    Part &P = b->parts[kind];
+    if (P.members.empty()) return FBP_OK;
+    // union arrays
+    std::vector<int64_t> fptr(1, 0);
+    std::vector<int32_t> fvars, fac_graph, var_graph;
+    std::vector<uint8_t> ftype;
+    std::vector<float> fparam, prior;
+    std::vector<int8_t> ev;
+    int32_t nv = 0, na = 0;
+    int64_t ne = 0;
+    for (size_t k = 0; k < P.members.size(); ++k) {
+        const fbp_graph_desc &d = graphs[P.members[k]];
+        P.var_off.push_back(nv);
+        P.fac_off.push_back(na);
+        P.edge_off.push_back((int32_t)ne);
+        for (int32_t a = 0; a < d.n_factors; ++a) {
+            for (int64_t e = d.factor_ptr[a]; e < d.factor_ptr[a + 1]; ++e) fvars.push_back(d.factor_vars[e] + nv);
+            fptr.push_back(ne + d.factor_ptr[a + 1]);
+            ftype.push_back(d.factor_type[a]);
+            fparam.push_back(d.factor_param[a]);
+            fac_graph.push_back((int32_t)k);
+        }
+        for (int32_t v = 0; v < d.n_vars; ++v) {
+            prior.push_back(d.prior_p1 ? d.prior_p1[v] : std::numeric_limits<float>::quiet_NaN());
+            ev.push_back(d.evidence ? d.evidence[v] : (int8_t)-1);
+            var_graph.push_back((int32_t)k);
+        }
+        nv += d.n_vars;
+        na += d.n_factors;
+        ne += d.factor_ptr[d.n_factors];
+        P.max_iters = std::max(P.max_iters, d.max_iters);
+    }
+    if (ne >= (int64_t)1 << 31) return fail(FBP_ERR_INVALID_ARG, "batch part too large (%lld edges)", (long long)ne);
+    int rc = fbp_graph_create(nv, na, fptr.data(), fvars.data(), ftype.data(), fparam.data(), prior.data(),
+                              ev.data(), alloc, P.stream, &P.g);
+    if (rc) return rc;
+    fbp_graph *g = P.g;
+    g->fac_graph = fac_graph;
+    const int32_t m = (int32_t)P.members.size();
+    // per-member state
+    std::vector<float> tol(m);
+    std::vector<int32_t> maxit(m);
+    for (int32_t k = 0; k < m; ++k) {
+        tol[k] = (float)graphs[P.members[k]].tol;
+        maxit[k] = graphs[P.members[k]].max_iters;
+    }
+    if ((rc = dalloc_n(g, &P.done, m)) || (rc = dalloc_n(g, &P.iters, m)) || (rc = dalloc_n(g, &P.active, 1)) ||
+        (rc = dalloc_n(g, &P.res, m)) || (rc = dalloc_n(g, &P.last_res, m)) ||
+        (rc = upload(g, &P.tol, tol.data(), tol.size())) || (rc = upload(g, &P.maxit, maxit.data(), maxit.size())))
+        return rc;
+    if (kind == kFlood) {
+        g->strategy = FBP_PARALL;
+        if ((rc = upload(g, &P.vgraph, var_graph.data(), var_graph.size())) ||
+            (rc = upload(g, &P.fgraph, fac_graph.data(), fac_graph.size())) || (rc = build_flood_plan(g)))
+            return rc;
+        if (!g->v2a && (rc = dalloc_n(g, &g->v2a, (size_t)g->h.ne))) return rc;
+        return FBP_OK;
+    }
+    // static parts: each member's own levels, merged by level index
+    const int halves = kind == kStatic2 ? 2 : 1;
+    std::vector<LevelSet> merged(halves);
+    for (int hf = 0; hf < halves; ++hf) {
+        std::vector<std::vector<int64_t>> lps(m);
+        std::vector<std::vector<int32_t>> les(m);
+        size_t nl = 0;
+        for (int32_t k = 0; k < m; ++k) {
+            const fbp_graph_desc &d = graphs[P.members[k]];
+            HostCSR h;
+            build_host_csr(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param, h);
+            std::vector<int64_t> rank;
+            rc = build_ranks(h, d.schedule, hf, rank);
+            if (rc) {
+                std::string msg = std::string("batch graph ") + std::to_string(P.members[k]) + ": " + fbp_last_error();
+                return fail(rc, "%s", msg.c_str());
+            }
+            dependency_levels(h, rank.data(), nullptr, h.ne, lps[k], les[k]);
+            nl = std::max(nl, lps[k].size() - 1);
+        }
+        LevelSet &ls = merged[hf];
+        ls.lp.assign(1, 0);
+        for (size_t L = 0; L < nl; ++L) {
+            for (int32_t k = 0; k < m; ++k) {
+                if (L + 1 >= lps[k].size()) continue;
+                for (int64_t i = lps[k][L]; i < lps[k][L + 1]; ++i) ls.le.push_back(les[k][i] + P.edge_off[k]);
+            }
+            ls.lp.push_back((int64_t)ls.le.size());
+        }
+    }
+    free_levels(g);
+    g->halves = std::move(merged);
+    g->strategy = kind == kStatic2 ? FBP_TOPO_FB : FBP_TOPO;
+    for (auto &ls : g->halves)
+        if ((rc = upload_levels(g, ls))) return rc;
+    if (!g->a2v[1] && (rc = dalloc_n(g, &g->a2v[1], (size_t)g->h.ne))) return rc;
+    return FBP_OK;
+}
+
+int part_reset_state(Part &P)
+{
+    fbp_graph *g = P.g;
+    const size_t m = P.members.size();
+    cudaStream_t s = g->stream;
+    cudaError_t e = cudaMemsetAsync(P.done, 0, sizeof(int32_t) * m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.iters, 0, sizeof(int32_t) * m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.res, 0, sizeof(unsigned) * m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.last_res, 0, sizeof(unsigned) * m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.active, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, s);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch reset: %s", cudaGetErrorString(e));
+    return FBP_OK;
+}
+
+// Enqueue the static part's run (one persistent launch); checked later.
+int launch_static(fbp_batch *b, Part &P)
+{
+    fbp_graph *g = P.g;
+    int rc = ensure_res_cap(g, std::max(P.max_iters, 1));
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(P.max_iters, 1), g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    if ((rc = part_reset_state(P))) return rc;
+    EngineArgs A = engine_args(g);
+    A.res = g->d_res_it;
+    A.max_iters = P.max_iters;
+    A.tol = 0.f;
+    A.batch = P.ctl();
+    if (P.max_iters <= 0) return FBP_OK;
+    g->engine_grid = b->tuning.engine_grid;
+    g->engine_cluster = b->tuning.engine_cluster;
+    int grid = 1, cluster = 0;
+    engine_shape(g, &grid, &cluster);
+    e = launch_engine(A, grid, cluster, g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "engine launch: %s", cudaGetErrorString(e));
+    b->stats.kernel_launches += 1;
+    return FBP_OK;
+}
+
+// The flooding part: iterations queued in growing batches on its stream.
+int run_flood(fbp_batch *b, Part &P)
+{
+    fbp_graph *g = P.g;
+    int rc = part_reset_state(P);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    rc = ensure_res_cap(g, std::max(P.max_iters, 1));
+    if (rc) return rc;
+    FloodPlanDev F = g->flood;
+    F.vgraph = P.vgraph;
+    F.fgraph = P.fgraph;
+    F.batch = P.ctl();
+    IterCtl ctl{g->d_res, g->d_guards};
+    int32_t next = 1, batch = 4;
+    bool done = false;
+    while (next <= P.max_iters && !done) {
+        const int32_t last = std::min(P.max_iters, next + batch - 1);
+        for (int32_t it = next; it <= last; ++it) {
+            flood_iteration(g->d, F, g->a2v[g->cur], g->v2a, ctl, g->flood_staged, it, 0.f, g->d_res_it, g->d_out,
+                            g->stream);
+            b->stats.kernel_launches += 5;
+        }
+        e = cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "flood batch: %s", cudaGetErrorString(e));
+        done = g->h_out[0] != 0;
+        next = last + 1;
+        batch = std::min(batch * 2, 64);
+    }
+    return FBP_OK;
+}
+
+int collect(fbp_batch *b, Part &P, int32_t *iters_out, double *residual_out, int32_t *status_out, int *all_ok)
+{
+    const size_t m = P.members.size();
+    std::vector<int32_t> done(m), iters(m);
+    std::vector<unsigned> res(m);
+    fbp_graph *g = P.g;
+    cudaError_t e = cudaMemcpyAsync(done.data(), P.done, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iters.data(), P.iters, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res.data(), P.last_res, sizeof(unsigned) * m, cudaMemcpyDeviceToHost, g->stream);
+    unsigned long long guards = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&guards, g->d_guards, sizeof guards, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch collect: %s", cudaGetErrorString(e));
+    b->stats.guards += (int64_t)guards;
+    const int halves = std::max<int>(1, (int)g->halves.size());
+    for (size_t k = 0; k < m; ++k) {
+        const int32_t i = P.members[k];
+        float r;
+        std::memcpy(&r, &res[k], sizeof r);
+        const int st = done[k] == 1 ? FBP_OK : FBP_NOT_CONVERGED;
+        if (st != FBP_OK) *all_ok = 0;
+        if (iters_out) iters_out[i] = iters[k];
+        if (residual_out) residual_out[i] = (double)r;
+        if (status_out) status_out[i] = st;
+        const int64_t e_k = (k + 1 < m ? P.edge_off[k + 1] : g->h.ne) - P.edge_off[k];
+        b->stats.updates += (int64_t)iters[k] * e_k * (g->strategy == FBP_PARALL ? 1 : halves);
+        b->stats.iters = std::max(b->stats.iters, iters[k]);
+    }
+    return FBP_OK;
+}
+
+}  // namespace
+
+extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
+                                void *cuda_stream, fbp_batch **out)
+{
+    if (!out || n_graphs < 0 || (n_graphs > 0 && !graphs)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        const fbp_graph_desc &d = graphs[i];
+        int rc = check_graph_args(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param,
+                                  d.prior_p1, d.evidence);
+        if (rc) {
+            std::string msg = std::string("batch graph ") + std::to_string(i) + ": " + fbp_last_error();
+            return fail(rc, "%s", msg.c_str());
+        }
+        if (d.schedule.strategy == FBP_RESIDUAL || d.schedule.strategy < 0 || d.schedule.strategy > FBP_CUSTOM_RANK)
+            return fail(FBP_ERR_INVALID_ARG, "batch graph %d: strategy %d not supported in a batch", i,
+                        d.schedule.strategy);
+        if (d.max_iters < 0 || !(d.tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "batch graph %d: bad max_iters/tol", i);
+    }
+    fbp_batch *b = new fbp_batch();
+    b->n = n_graphs;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->part_of.resize(n_graphs);
+    b->slot_of.resize(n_graphs);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        const int k = kind_of(graphs[i].schedule.strategy);
+        b->part_of[i] = k;
+        b->slot_of[i] = (int32_t)b->parts[k].members.size();
+        b->parts[k].members.push_back(i);
+        b->nv.push_back(graphs[i].n_vars);
+        b->ne.push_back((int32_t)graphs[i].factor_ptr[graphs[i].n_factors]);
+    }
+    int rc = FBP_OK;
+    bool first = true;
+    for (int k = 0; k < kParts && !rc; ++k) {
+        Part &P = b->parts[k];
+        if (P.members.empty()) continue;
+        if (first) {
+            P.stream = b->stream;
+            first = false;
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) rc = fail(FBP_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+            P.own_stream = true;
+        }
+        if (!rc) rc = build_part(b, k, graphs, alloc);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaEventCreate(&b->ev0);
+    if (!rc && e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    for (int k = 0; k < kParts && !rc && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->evp[k], cudaEventDisableTiming);
+    if (!rc && e != cudaSuccess) rc = fail(FBP_ERR_CUDA, "events: %s", cudaGetErrorString(e));
+    if (!rc) {
+        size_t mx = 1;
+        for (auto &P : b->parts)
+            if (P.g) mx = std::max(mx, (size_t)std::max<int64_t>(P.g->h.nv, 2 * (int64_t)P.g->h.ne));
+        e = cudaMalloc(&b->scratch, mx * sizeof(float));
+        if (e != cudaSuccess) rc = fail(FBP_ERR_OOM, "batch scratch: %s", cudaGetErrorString(e));
+        b->scratch_n = mx;
+    }
+    if (rc) {
+        std::string keep = fbp_last_error();
+        fbp_batch_destroy(b);
+        return fail(rc, "%s", keep.c_str());
+    }
+    *out = b;
+    return FBP_OK;
+}
+
+extern "C" int fbp_batch_run(fbp_batch *b, int32_t *iters_out, double *residual_out, int32_t *status_out)
+{
+    if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
+    b->stats = fbp_stats{};
+    cudaError_t e = cudaEventRecord(b->ev0, b->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    // side streams start after ev0
+    for (auto &P : b->parts)
+        if (P.g && P.stream != b->stream) cudaStreamWaitEvent(P.stream, b->ev0, 0);
+    int rc = FBP_OK;
+    for (int k : {kStatic1, kStatic2})
+        if (b->parts[k].g && !rc) rc = launch_static(b, b->parts[k]);
+    if (!rc && b->parts[kFlood].g) rc = run_flood(b, b->parts[kFlood]);
+    if (rc) return rc;
+    for (int k : {kStatic1, kStatic2}) {
+        Part &P = b->parts[k];
+        if (!P.g || P.max_iters <= 0) continue;
+        rc = engine_check(P.g);
+        if (rc) return rc;
+        const int32_t it = P.g->h_out[0];
+        P.g->cur ^= (it * (int)P.g->halves.size()) & 1;
+    }
+    for (int k = 0; k < kParts; ++k) {
+        Part &P = b->parts[k];
+        if (P.g && P.stream != b->stream) {
+            cudaEventRecord(b->evp[k], P.stream);
+            cudaStreamWaitEvent(b->stream, b->evp[k], 0);
+        }
+    }
+    e = cudaEventRecord(b->ev1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->ev1);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    b->stats.run_ms = ms;
+    int all_ok = 1;
+    for (auto &P : b->parts)
+        if (P.g && (rc = collect(b, P, iters_out, residual_out, status_out, &all_ok))) return rc;
+    return all_ok ? FBP_OK : FBP_NOT_CONVERGED;
+}
+
+extern "C" int fbp_batch_marginals(const fbp_batch *b, int32_t graph, float *out_p1, int out_is_device)
+{
+    if (!b || graph < 0 || graph >= b->n) return fail(FBP_ERR_INVALID_ARG, "bad graph index");
+    const Part &P = b->parts[b->part_of[graph]];
+    const int32_t k = b->slot_of[graph];
+    if (b->nv[graph] == 0) return FBP_OK;
+    if (!out_p1) return fail(FBP_ERR_INVALID_ARG, "NULL output");
+    int rc = fbp_marginals(P.g, b->scratch, 1);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(out_p1, b->scratch + P.var_off[k], sizeof(float) * b->nv[graph],
+                                    out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P.g->stream);
+    if (e == cudaSuccess && !out_is_device) e = cudaStreamSynchronize(P.g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return FBP_OK;
+}
+
+extern "C" int fbp_batch_messages_export(const fbp_batch *b, int32_t graph, float *a2v)
+{
+    if (!b || graph < 0 || graph >= b->n) return fail(FBP_ERR_INVALID_ARG, "bad graph index");
+    const Part &P = b->parts[b->part_of[graph]];
+    const int32_t k = b->slot_of[graph];
+    if (b->ne[graph] == 0) return FBP_OK;
+    if (!a2v) return fail(FBP_ERR_INVALID_ARG, "NULL output");
+    fbp_graph *g = P.g;
+    launch_decode_pairs(g->a2v[g->cur] + P.edge_off[k], b->scratch, b->ne[graph], g->stream);
+    cudaError_t e = cudaMemcpyAsync(a2v, b->scratch, sizeof(float) * 2 * b->ne[graph], cudaMemcpyDeviceToHost,
+                                    g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return FBP_OK;
+}
+
+extern "C" int fbp_batch_reset(fbp_batch *b)
+{
+    if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
+    for (auto &P : b->parts) {
+        if (!P.g) continue;
+        int rc = fbp_messages_reset(P.g);
+        if (rc) return rc;
+    }
+    return FBP_OK;
+}
+
+extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
+{
+    if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
+    b->tuning = t ? *t : fbp_batch_tuning{0, 0};
+    if (b->tuning.engine_grid < 0 ||
+        (b->tuning.engine_cluster != 0 && b->tuning.engine_cluster != 1 && b->tuning.engine_cluster != 8 &&
+         b->tuning.engine_cluster != 16))
+        return fail(FBP_ERR_INVALID_ARG, "bad tuning");
+    return FBP_OK;
+}
+
+extern "C" int fbp_batch_get_stats(const fbp_batch *b, fbp_stats *out)
+{
+    if (!b || !out) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    *out = b->stats;
+    return FBP_OK;
+}
+
+extern "C" void fbp_batch_destroy(fbp_batch *b)
+{
+    if (!b) return;
+    for (auto &P : b->parts) {
+        if (P.g) fbp_graph_destroy(P.g);
+        if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
+    }
+    if (b->scratch) cudaFree(b->scratch);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    for (auto &ev : b->evp)
+        if (ev) cudaEventDestroy(ev);
+    delete b;
+}

@@ -163,9 +163,13 @@ __device__ __forceinline__ void run_lane(const Pre &s, const EngineArgs &A, cons
     const int q = s.rec.x;
     const int pk = s.rec.y;
     const bool tgt = q >= 0 && ((pk >> 14) & 1);
+    const int graph = pk >> 15;
+    // a graph of a batch that has stopped keeps its messages: its lanes only
+    // carry them over into the next buffer
+    const bool frozen = A.batch.n_graphs > 0 && q >= 0 && __ldcg(A.batch.done + graph) != 0;
     const float old = tgt ? __ldcg(cur + q) : 1.f;
     P2 m{1.f, 1.f};
-    if (q >= 0) {
+    if (q >= 0 && !frozen) {
         float r[kPre];
 #pragma unroll
         for (int u = 0; u < kPre; ++u)
@@ -199,19 +203,55 @@ __device__ __forceinline__ void run_lane(const Pre &s, const EngineArgs &A, cons
     const int lane = threadIdx.x & 31;
     sm[lane] = m;
     __syncwarp();
+    float d = 0.f;
     if (tgt) {
-        const int first = pk & 31, n = (pk >> 5) & 63, type = (pk >> 11) & 7;
-        const float p = __int_as_float(s.rec.z);
-        const P2 mu = a2v_unified(type, p, n, lane - first, [&](int j) { return sm[first + j]; });
-        bool gd = false;
-        const float r = enc_fast(mu, gd);
-        ng += gd;
-        const float d = delta_p1_fast(r, old);
-        rmax = fmaxf(rmax, d);
-        __stcg(nxt + q, r);
-        if (A.dres) A.dres[q] = d;
+        if (frozen) {
+            __stcg(nxt + q, old);
+        } else {
+            const int first = pk & 31, n = (pk >> 5) & 63, type = (pk >> 11) & 7;
+            const float p = __int_as_float(s.rec.z);
+            const P2 mu = a2v_unified(type, p, n, lane - first, [&](int j) { return sm[first + j]; });
+            bool gd = false;
+            const float r = enc_fast(mu, gd);
+            ng += gd;
+            d = delta_p1_fast(r, old);
+            rmax = fmaxf(rmax, d);
+            __stcg(nxt + q, r);
+            if (A.dres) A.dres[q] = d;
+        }
+    }
+    if (A.batch.n_graphs > 0) {
+        // per-graph residual: one atomic per graph present in the warp
+        const unsigned grp = __match_any_sync(0xffffffffu, q >= 0 ? graph : -1);
+        const unsigned bits = __reduce_max_sync(grp, __float_as_uint(d));
+        if (q >= 0 && lane == __ffs(grp) - 1 && bits) atomicMax(A.batch.res + graph, bits);
     }
     __syncwarp();
+}
+
+// End of one iteration of a batch (one block): every running graph records
+// its residual and iteration count and stops at its tolerance or its own
+// iteration limit; the count of graphs still running is published.
+__device__ __forceinline__ void batch_iteration_end(const BatchCtl &B, int it)
+{
+    __shared__ int s_active;
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    int act = 0;
+    for (int gi = threadIdx.x; gi < B.n_graphs; gi += blockDim.x) {
+        if (__ldcg(B.done + gi)) continue;
+        const unsigned r = __ldcg(B.res + gi);
+        B.res[gi] = 0u;
+        B.last_res[gi] = r;
+        B.iters[gi] = it;
+        if (__uint_as_float(r) < __ldg(B.tol + gi)) B.done[gi] = 1;
+        else if (it >= __ldg(B.max_iters + gi)) B.done[gi] = 2;
+        else ++act;
+    }
+    act = __reduce_add_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0 && act) atomicAdd(&s_active, act);
+    __syncthreads();
+    if (threadIdx.x == 0) *B.active = s_active;
 }
 
 __device__ __forceinline__ LevelPlanDev plan_at(const EngineArgs &A, int h)
@@ -308,6 +348,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine(EngineArgs A)
             nxt = t;
         }
         if (failed) break;
+        if (A.batch.n_graphs > 0) {
+            if (blockIdx.x == 0) batch_iteration_end(A.batch, it);
+            if (kCluster) {
+                cluster_arrive();
+                cluster_wait();
+            } else {
+                grid_arrive(A.bar);
+                target += gridDim.x;
+                if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
+                    failed = 1;
+                    break;
+                }
+            }
+            if (*(volatile int *)A.batch.active == 0) {
+                status = 0;
+                break;
+            }
+            continue;
+        }
         const float r = __uint_as_float(*(volatile unsigned *)(A.res + (it - 1)));
         if (r < A.tol) {
             status = 0;

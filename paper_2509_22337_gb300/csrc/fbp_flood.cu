@@ -28,6 +28,12 @@ namespace {
 
 __device__ __forceinline__ XP xp_one() { return XP{1.f, 1.f, 0, 0, 0, 0}; }
 
+// In a batch, rows and factors of graphs that have stopped are skipped.
+__device__ __forceinline__ bool var_frozen(const FloodPlanDev &F, int v)
+{
+    return F.batch.n_graphs > 0 && __ldcg(F.batch.done + __ldg(F.vgraph + v)) != 0;
+}
+
 // Multiply entry (m, e, z) by x in [0, 1]: exact zeros are counted; the
 // mantissa is renormalised into [1/2, 1) only when the product falls below
 // 2^-60, so the common case is one multiply and one compare.
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(256) k_hub_partials(const DevGraph g, FloodPla
     if (*(volatile const int *)F.done) return;
     const int c = blockIdx.x;
     const int4 ch = __ldg(F.hub + c);  // {var, begin, end, first chunk of the row}
+    if (var_frozen(F, ch.x)) return;   // block-uniform
     XP t = xp_one();
     for (int k0 = ch.y + threadIdx.x; k0 < ch.z; k0 += 4 * blockDim.x) {
         int e[4];
@@ -171,12 +178,12 @@ __global__ void __launch_bounds__(256) k_hub_partials(const DevGraph g, FloodPla
 
 // Variables of degree 1 and 2 (most of a derivation graph: every rule's
 // derivation variable has degree 2): one thread each, few registers.
-__global__ void __launch_bounds__(256) k_v2a_lean(const DevGraph g, const float *__restrict__ a2v,
-                                                  float *__restrict__ v2a, const int *done)
+__global__ void __launch_bounds__(256) k_v2a_lean(const DevGraph g, const FloodPlanDev F,
+                                                  const float *__restrict__ a2v, float *__restrict__ v2a)
 {
-    if (*(volatile const int *)done) return;
+    if (*(volatile const int *)F.done) return;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv) return;
+    if (v >= g.nv || var_frozen(F, v)) return;
     const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
     if (d == 0 || d > 2) return;
     const P2 f = dec(__ldg(g.phi + v));
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
         const int i = b * blockDim.x + threadIdx.x;
         if (i >= F.n_small) return;
         const int v = __ldg(F.small + i);
+        if (var_frozen(F, v)) return;
         const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
         const P2 f = dec(__ldg(g.phi + v));
         bool gd = false;
@@ -238,6 +246,7 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
         const int w = bm * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
         if (w >= F.n_medium) return;
         const int v = __ldg(F.medium + w);
+        if (var_frozen(F, v)) return;
         const int lo = __ldg(g.vptr + v), hi = __ldg(g.vptr + v + 1);
         // at most kFloodMediumMax / 32 = 8 entries per lane, all loads issued first
         int e[kFloodMediumMax / 32];
@@ -259,6 +268,7 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
     // hub chunk: combine the row's chunk partials, then every entry of this chunk
     const int c = bm - F.nb_medium;
     const int4 ch = __ldg(F.hub + c);
+    if (var_frozen(F, ch.x)) return;  // block-uniform
     const int c0 = ch.w, nc = __ldg(F.hub_nchunks + c);
     __shared__ XP s_tot;
     if (threadIdx.x < 32) {
@@ -376,11 +386,11 @@ __device__ __forceinline__ void factor_linear(int type, float p, int n, const fl
     }
 }
 
-__global__ void __launch_bounds__(256) k_a2v_rows(const DevGraph g, const float *__restrict__ v2a,
-                                                  float *__restrict__ a2v, IterCtl ctl, int staged,
-                                                  const int *done)
+__global__ void __launch_bounds__(256) k_a2v_rows(const DevGraph g, const FloodPlanDev F,
+                                                  const float *__restrict__ v2a, float *__restrict__ a2v,
+                                                  IterCtl ctl, int staged)
 {
-    if (*(volatile const int *)done) return;
+    if (*(volatile const int *)F.done) return;
     extern __shared__ float s_dyn[];
     const int a0 = blockIdx.x * blockDim.x, a1 = min(a0 + (int)blockDim.x, g.na);
     const int e0 = __ldg(g.fptr + a0), e1 = __ldg(g.fptr + a1);
@@ -397,7 +407,9 @@ __global__ void __launch_bounds__(256) k_a2v_rows(const DevGraph g, const float 
     float rmax = 0.f;
     unsigned long long ng = 0;
     const int a = a0 + threadIdx.x;
-    if (a < a1) {
+    const int graph = (F.batch.n_graphs > 0 && a < a1) ? __ldg(F.fgraph + a) : -1;
+    const bool frozen = graph >= 0 && __ldcg(F.batch.done + graph) != 0;
+    if (a < a1 && !frozen) {
         const int lo = __ldg(g.fptr + a), n = __ldg(g.fptr + a + 1) - lo;
         const int type = __ldg(g.ftype + a);
         const float p = __ldg(g.fparam + a);
@@ -421,8 +433,43 @@ __global__ void __launch_bounds__(256) k_a2v_rows(const DevGraph g, const float 
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) a2v[e0 + i] = s_io[i];
     }
     if (ng) atomicAdd(ctl.guards, ng);
+    if (F.batch.n_graphs > 0) {
+        // per-graph residual: one atomic per graph present in the warp
+        const unsigned grp = __match_any_sync(0xffffffffu, graph);
+        const unsigned bits = __reduce_max_sync(grp, __float_as_uint(rmax));
+        if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) atomicMax(F.batch.res + graph, bits);
+        return;
+    }
     const float bm = block_max(rmax);
     if (threadIdx.x == 0 && bm > 0.f) atomicMax(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
+}
+
+// End of an iteration of a batch: per-graph bookkeeping as in the persistent
+// engine; the run is done when no graph is running.
+__global__ void k_flood_batch_check(BatchCtl B, int it, int *ctl)
+{
+    if (*(volatile int *)ctl) return;
+    __shared__ int s_active;
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    int act = 0;
+    for (int gi = threadIdx.x; gi < B.n_graphs; gi += blockDim.x) {
+        if (B.done[gi]) continue;
+        const unsigned r = B.res[gi];
+        B.res[gi] = 0u;
+        B.last_res[gi] = r;
+        B.iters[gi] = it;
+        if (__uint_as_float(r) < B.tol[gi]) B.done[gi] = 1;
+        else if (it >= B.max_iters[gi]) B.done[gi] = 2;
+        else ++act;
+    }
+    act = __reduce_add_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0 && act) atomicAdd(&s_active, act);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl[1] = it;
+        if (s_active == 0) ctl[0] = 1;
+    }
 }
 
 // End of an iteration: the residual of iteration `it` is the max over the
@@ -454,15 +501,16 @@ void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float
 {
     FloodPlanDev P = F;
     P.done = done;
-    if (g.nv > 0) k_v2a_lean<<<(g.nv + 255) / 256, 256, 0, s>>>(g, a2v, v2a, done);
+    if (g.nv > 0) k_v2a_lean<<<(g.nv + 255) / 256, 256, 0, s>>>(g, P, a2v, v2a);
     if (P.n_hub > 0) k_hub_partials<<<P.n_hub, 256, 0, s>>>(g, P, a2v);
     const int nb = P.nb_small + P.nb_medium + P.n_hub;
     if (nb > 0) k_v2a_rest<<<nb, 256, 0, s>>>(g, P, a2v, v2a);
     if (g.na > 0) {
         const int blocks = (g.na + 255) / 256;
-        k_a2v_rows<<<blocks, 256, flood_smem_bytes(staged), s>>>(g, v2a, a2v, ctl, staged, done);
+        k_a2v_rows<<<blocks, 256, flood_smem_bytes(staged), s>>>(g, P, v2a, a2v, ctl, staged);
     }
-    k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, it, tol, done);
+    if (P.batch.n_graphs > 0) k_flood_batch_check<<<1, 1024, 0, s>>>(P.batch, it, done);
+    else k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, it, tol, done);
 }
 
 size_t flood_smem_bytes(int staged) { return (size_t)staged * (2 + kAccFloats) * sizeof(float); }

@@ -29,6 +29,10 @@ struct FloodPlanDev {
     const int32_t *hub_nchunks = nullptr;  // [n_hub] chunks of the chunk's row
     XP *agg = nullptr;                 // [n_hub] partial product of each chunk
     const int *done = nullptr;         // set once the run has converged
+    // batched graphs: graph of each variable and factor; per-graph state
+    const int32_t *vgraph = nullptr;
+    const int32_t *fgraph = nullptr;
+    BatchCtl batch;
 };
 
 // One flooding iteration (number `it`): phase 1 over every variable row,

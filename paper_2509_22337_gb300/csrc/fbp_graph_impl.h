@@ -1,0 +1,112 @@
+// Internal state of a graph handle and the host helpers shared by the
+// single-graph C ABI (fbp_host.cpp) and the batched form (fbp_batch.cpp).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "fbp.h"
+#include "fbp_flood.h"
+#include "fbp_internal.h"
+#include "fbp_sched.h"
+
+using fbp::DevGraph;
+using fbp::FloodPlanDev;
+using fbp::HostCSR;
+using fbp::LevelPlanDev;
+
+struct LevelSet {                    // one level list (one half of TOPO_FB)
+    std::vector<int64_t> lp;         // level_ptr (Algorithm 2's S)
+    std::vector<int32_t> le;         // level_edges (canonical order)
+    // engine plan (device)
+    int4 *d_lanes = nullptr;
+    int2 *d_lrow = nullptr;
+    int32_t *d_lane_ptr = nullptr, *d_big = nullptr, *d_big_ptr = nullptr;
+    int2 *d_vel = nullptr;
+    int32_t max_lanes = 0;           // widest level, in lanes
+    int64_t n_lanes = 0;
+};
+
+struct fbp_graph {
+    HostCSR h;                        // host CSR + transpose (also used by scheduling)
+    std::vector<float> prior;
+    std::vector<int8_t> evidence;
+    std::vector<float> phi;           // rho-encoded unary potentials
+    DevGraph d;
+    cudaStream_t stream = nullptr;
+    fbp_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> owned;
+    // messages
+    float *a2v[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *v2a = nullptr;
+    float *pairs = nullptr;           // export/import staging [2E]
+    float *p1 = nullptr;              // marginals [V]
+    // schedule
+    int strategy = FBP_PARALL;
+    std::vector<LevelSet> halves;     // 1 (static) or 2 (TOPO_FB)
+    // residual strategy working state
+    float *dres = nullptr;            // [E] |delta m1| of the last write
+    int32_t *d_act = nullptr;         // [E] active edges (residual)
+    // persistent engine
+    int4 *erow = nullptr;             // [E] row record of each edge's variable
+    unsigned *d_res_it = nullptr;     // [res_cap] residual bits per iteration
+    int32_t res_cap = 0;
+    unsigned *d_bar = nullptr;        // [2] barrier words
+    int32_t *d_out = nullptr;         // [4] engine outputs
+    int32_t *h_out = nullptr;         // pinned copy
+    long long spin_limit = 4000000000LL;
+    int engine_grid = 0;              // 0 = automatic
+    int engine_cluster = 0;           // 0 = automatic, 1 = never, 8 or 16 = cluster size
+    int use_engine = 1;
+    // flooding plan
+    FloodPlanDev flood;
+    bool flood_ready = false;
+    int flood_staged = 0;
+    // per-iteration control
+    unsigned *d_res = nullptr;
+    unsigned long long *d_guards = nullptr;
+    unsigned *h_res = nullptr;        // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    fbp_stats stats{};
+    // batched union graphs: the batch member of every factor (empty for a
+    // single graph); lane records carry it in bits 15.. of their packed word
+    std::vector<int32_t> fac_graph;
+};
+
+
+namespace fbp {
+
+int dalloc(fbp_graph *g, void **p, size_t bytes);
+void dfree(fbp_graph *g, void *p);
+template <class T>
+int dalloc_n(fbp_graph *g, T **p, size_t n)
+{
+    return dalloc(g, (void **)p, n * sizeof(T));
+}
+template <class T>
+int upload(fbp_graph *g, T **p, const T *src, size_t n)
+{
+    int rc = dalloc_n(g, p, n);
+    if (rc) return rc;
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(*p, src, n * sizeof(T), cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+    }
+    return FBP_OK;
+}
+void free_levels_one(fbp_graph *g, LevelSet &ls);
+void free_levels(fbp_graph *g);
+int upload_levels(fbp_graph *g, LevelSet &ls);
+int build_flood_plan(fbp_graph *g);
+int ensure_res_cap(fbp_graph *g, int32_t n);
+LevelPlanDev plan_of(const LevelSet &ls);
+void engine_shape(const fbp_graph *g, int *grid, int *cluster);
+EngineArgs engine_args(fbp_graph *g);
+int engine_check(fbp_graph *g);
+int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars, const uint8_t *ftype,
+                     const float *fparam, const float *prior, const int8_t *evidence);
+int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_out, double *residual_out);
+
+}  // namespace fbp

@@ -7,6 +7,7 @@
 #include "fbp_internal.h"
 #include "fbp_flood.h"
 #include "fbp_sched.h"
+#include "fbp_graph_impl.h"
 
 #include <algorithm>
 #include <cmath>
@@ -65,64 +66,7 @@ float phi_of(float prior, int8_t ev)
 // ---------------------------------------------------------------------------
 // graph handle
 // ---------------------------------------------------------------------------
-struct LevelSet {                    // one level list (one half of TOPO_FB)
-    std::vector<int64_t> lp;         // level_ptr (Algorithm 2's S)
-    std::vector<int32_t> le;         // level_edges (canonical order)
-    // engine plan (device)
-    int4 *d_lanes = nullptr;
-    int2 *d_lrow = nullptr;
-    int32_t *d_lane_ptr = nullptr, *d_big = nullptr, *d_big_ptr = nullptr;
-    int2 *d_vel = nullptr;
-    int32_t max_lanes = 0;           // widest level, in lanes
-    int64_t n_lanes = 0;
-};
-
-struct fbp_graph {
-    HostCSR h;                        // host CSR + transpose (also used by scheduling)
-    std::vector<float> prior;
-    std::vector<int8_t> evidence;
-    std::vector<float> phi;           // rho-encoded unary potentials
-    DevGraph d;
-    cudaStream_t stream = nullptr;
-    fbp_allocator alloc{};
-    bool has_alloc = false;
-    std::vector<void *> owned;
-    // messages
-    float *a2v[2] = {nullptr, nullptr};
-    int cur = 0;
-    float *v2a = nullptr;
-    float *pairs = nullptr;           // export/import staging [2E]
-    float *p1 = nullptr;              // marginals [V]
-    // schedule
-    int strategy = FBP_PARALL;
-    std::vector<LevelSet> halves;     // 1 (static) or 2 (TOPO_FB)
-    // residual strategy working state
-    float *dres = nullptr;            // [E] |delta m1| of the last write
-    int32_t *d_act = nullptr;         // [E] active edges (residual)
-    // persistent engine
-    int4 *erow = nullptr;             // [E] row record of each edge's variable
-    unsigned *d_res_it = nullptr;     // [res_cap] residual bits per iteration
-    int32_t res_cap = 0;
-    unsigned *d_bar = nullptr;        // [2] barrier words
-    int32_t *d_out = nullptr;         // [4] engine outputs
-    int32_t *h_out = nullptr;         // pinned copy
-    long long spin_limit = 4000000000LL;
-    int engine_grid = 0;              // 0 = automatic
-    int engine_cluster = 0;           // 0 = automatic, 1 = never, 8 or 16 = cluster size
-    int use_engine = 1;
-    // flooding plan
-    FloodPlanDev flood;
-    bool flood_ready = false;
-    int flood_staged = 0;
-    // per-iteration control
-    unsigned *d_res = nullptr;
-    unsigned long long *d_guards = nullptr;
-    unsigned *h_res = nullptr;        // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    fbp_stats stats{};
-};
-
-namespace {
+namespace fbp {
 
 int dalloc(fbp_graph *g, void **p, size_t bytes)
 {
@@ -141,21 +85,6 @@ int dalloc(fbp_graph *g, void **p, size_t bytes)
         }
     }
     g->owned.push_back(*p);
-    return FBP_OK;
-}
-
-template <class T>
-int dalloc_n(fbp_graph *g, T **p, size_t n)
-{
-    return dalloc(g, (void **)p, n * sizeof(T));
-}
-
-template <class T>
-int upload(fbp_graph *g, T **p, const T *src, size_t n)
-{
-    int rc = dalloc_n(g, p, n);
-    if (rc) return rc;
-    if (n) CUDA_TRY(cudaMemcpyAsync(*p, src, n * sizeof(T), cudaMemcpyHostToDevice, g->stream));
     return FBP_OK;
 }
 
@@ -241,8 +170,9 @@ int upload_levels(fbp_graph *g, LevelSet &ls)
             int32_t pb;
             std::memcpy(&pb, &h.fparam[a], sizeof pb);
             for (int32_t j = 0; j < n; ++j) {
+                const int32_t member = g->fac_graph.empty() ? 0 : g->fac_graph[a];
                 const int32_t pk = used | (n << 5) | ((int32_t)h.ftype[a] << 11) |
-                                   ((int32_t)((fmask[a] >> j) & 1u) << 14);
+                                   ((int32_t)((fmask[a] >> j) & 1u) << 14) | (member << 15);
                 const int32_t v = h.fvars[lo + j];
                 lanes.push_back(make_int4(lo + j, pk, pb, v));
                 lrow.push_back(make_int2(h.vptr[v], h.vptr[v + 1]));
@@ -388,7 +318,7 @@ int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t 
     return FBP_OK;
 }
 
-}  // namespace
+}  // namespace fbp
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -597,7 +527,7 @@ extern "C" int fbp_schedule_levels(const fbp_graph *g, int32_t *n_levels, int64_
 // ---------------------------------------------------------------------------
 // iteration driver
 // ---------------------------------------------------------------------------
-namespace {
+namespace fbp {
 
 int read_residual(fbp_graph *g, double *res)
 {
@@ -792,7 +722,7 @@ int run_per_level(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_ou
     return finish_run(g, it, res, status, iters_out, residual_out);
 }
 
-}  // namespace
+}  // namespace fbp
 
 extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
                        double *residual_out)

@@ -34,6 +34,18 @@ struct DevGraph {
     const float *phi = nullptr;       // [nv] unary potential, rho-encoded
 };
 
+// Per-graph convergence state of a batch of independent graphs run together.
+struct BatchCtl {
+    int32_t n_graphs = 0;              // 0: a single graph (the batch fields are unused)
+    int32_t *done = nullptr;           // [n_graphs] 0 running, 1 converged, 2 stopped at its max_iters
+    int32_t *iters = nullptr;          // [n_graphs] iterations run
+    unsigned *res = nullptr;           // [n_graphs] residual bits of the current iteration
+    unsigned *last_res = nullptr;      // [n_graphs] residual bits of the graph's last iteration
+    const float *tol = nullptr;        // [n_graphs]
+    const int32_t *max_iters = nullptr;// [n_graphs]
+    int32_t *active = nullptr;         // [1] graphs still running
+};
+
 // One half-iteration's levels, as the persistent engine reads them.
 struct LevelPlanDev {
     const int4 *lanes = nullptr;       // warp-packed lane records, level after level
@@ -60,6 +72,9 @@ struct EngineArgs {
     int32_t max_iters = 0;
     float tol = 0.f;
     long long spin_limit = 0;          // clock64 cycles one barrier may wait
+    // batched graphs (n_graphs > 0): every lane record carries its graph in
+    // bits 15.. of its packed word; each graph stops on its own residual.
+    BatchCtl batch;
 };
 
 int engine_block();

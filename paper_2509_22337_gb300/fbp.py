@@ -96,10 +96,7 @@ def load(path: str | None = None):
 
 def _bind_extras(L) -> None:
     """Batched and serving entry points (declared in include/fbp_batch.h)."""
-    try:
-        from . import fbp_batch as B
-    except ImportError:
-        return
+    from . import fbp_batch as B
     B.bind(L)
 
 

@@ -39,3 +39,16 @@ def test_invalid_graph_rejected(lib, mutate, msg):
         _create(g, **mutate(g))
     assert ei.value.code == F.FBP_ERR_INVALID_ARG
     assert msg in str(ei.value)
+
+
+def test_batch_rejects_bad_member_before_any_device_work(lib):
+    from paper_2509_22337_gb300 import fbp_batch as B
+    good = gen.fig1_example()
+    bad = gen.FactorGraph(5, good.factor_ptr, good.factor_vars.copy(), good.factor_type, good.factor_param,
+                          good.prior_p1, good.evidence)
+    bad.factor_vars[2] = 9
+    with pytest.raises(F.FbpError) as ei:
+        B.fbp_batch_create([good, bad], ["PARALL", "PARALL"], [10, 10], [0.0, 0.0], alloc=None, stream=0)
+    assert ei.value.code == F.FBP_ERR_INVALID_ARG and "batch graph 1" in str(ei.value)
+    with pytest.raises(F.FbpError):
+        B.fbp_batch_create([good], ["RESIDUAL"], [10], [0.0], alloc=None, stream=0)

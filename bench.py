@@ -42,6 +42,9 @@ WORKLOADS = {
                 "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
                 "PARALL to max change < 1e-6 or 500 iterations"),
     "tiny": ("tiny", "PARALL", 50, 0.0, "tiny derivation DAG, PARALL, exactly 50 iterations"),
+    "batched": ("batched", "MIXED", 0, 1e-6,
+                "512 graphs, sizes log-uniform in 1e3..1e5: even SmartFL-shaped (TOPO_FB, tol 1e-6, <= 100 "
+                "sweeps), odd BINGO-shaped (PARALL, tol 1e-6, <= 500 iterations); one batched run"),
 }
 
 
@@ -131,6 +134,98 @@ def algorithmic_bytes_flood(g):
     return 24 * E + 8 * V + 9 * A
 
 
+def run_batched(args, rank, world, local):
+    """The batched workload: one fbp_batch run of 512 graphs vs a per-graph loop."""
+    import torch
+    from paper_2509_22337_gb300 import autotune, fbp_batch as BB, gen
+    from paper_2509_22337_gb300 import fbp as F
+
+    graphs = gen.batched_mix(n_graphs=args.batch_graphs, seed=4 + 1000 * rank)
+    sch = ["TOPO_FB" if i % 2 == 0 else "PARALL" for i in range(len(graphs))]
+    mi = [100 if s == "TOPO_FB" else 500 for s in sch]
+    tol = [1e-6] * len(graphs)
+    stream = torch.cuda.current_stream()
+    B = BB.Batch(graphs, sch, mi, tol, stream=stream)
+    tuning = autotune.tune_batch(B, graphs, sch)
+    for _ in range(args.warmup):
+        B.reset()
+        B.run()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    times, upd = [], 0
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            B.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.run()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            upd += B.stats()["updates"]
+    st = B.stats()
+    total = float(sum(times))
+    # the per-graph launch loop on the same GPU (graphs resident, one pass)
+    Gs = [F.Graph(g, s, stream=stream) for g, s in zip(graphs, sch)]
+    for G, m in zip(Gs, mi):
+        G.run(1, 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop_upd = 0
+    for G, m in zip(Gs, mi):
+        G.reset()
+        G.run(m, 1e-6)
+        loop_upd += G.stats()["updates"]
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    for G in Gs:
+        G.close()
+    # end to end: batch creation from host arrays, run, every marginal to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B2 = BB.Batch(graphs, sch, mi, tol, stream=stream)
+    B2.tune(**tuning)
+    B2.run()
+    for i in range(len(graphs)):
+        B2.marginals(i)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_upd = B2.stats()["updates"]
+    B2.close()
+    h2d = sum(g.nbytes() for g in graphs)
+    d2h = sum(4 * g.n_vars for g in graphs)
+    t_max, tot = total, upd
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([float(upd)], device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tot = u.item()
+    n = len(graphs)
+    if rank == 0:
+        line = {
+            "metric": "BP message updates/s", "value": round(tot / t_max, 1), "unit": "msg_updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched", "desc": WORKLOADS["batched"][4], "n_graphs": n,
+                       "n_vars": sum(g.n_vars for g in graphs), "n_edges": sum(g.n_edges for g in graphs),
+                       "tuning": tuning, "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+            "graphs_per_s": round(n * world * args.steps / t_max, 2),
+            "per_graph_loop": {"graphs_per_s": round(n / loop_s, 2), "ms": round(loop_s * 1e3, 2),
+                               "msg_updates_per_s": round(loop_upd / loop_s, 1)},
+            "speedup_vs_loop": round((loop_s / n) / (t_max / (n * args.steps * world)), 2),
+            "max_iters_run": st["iters"],
+            "e2e": {"value": round(e2e_upd / e2e_s, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_s * 1e3, 2)},
+            "gpu_launches": int(st["kernel_launches"] * args.steps), "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    B.close()
+
+
 def run_gpu(args):
     import torch
 
@@ -147,6 +242,11 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     F.load()
+    if args.workload == "batched":
+        run_batched(args, rank, world, local)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     _, strategy, max_iters, tol, desc = WORKLOADS[args.workload]
     g = make_graph(args.workload)
     stream = torch.cuda.current_stream()
@@ -339,6 +439,7 @@ def main():
     ap.add_argument("--workload", default="smartfl200k", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -188,8 +188,15 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  *                      engine; 0: one launch per level (reference path).
  * FBP_OPT_ENGINE_CLUSTER 0 (default): automatic; 1: never run the engine as
  *                      one thread-block cluster; 8 or 16: always, with that
- *                      cluster size. */
-enum { FBP_OPT_SPIN_LIMIT = 1, FBP_OPT_ENGINE_GRID = 2, FBP_OPT_ENGINE = 3, FBP_OPT_ENGINE_CLUSTER = 4 };
+ *                      cluster size.
+ * FBP_OPT_FLOOD_HUB_MIN  flooding: variables with more incident factors than
+ *                      this (8..256, default 256) are split over blocks.
+ * FBP_OPT_FLOOD_CHUNK  flooding: entries of such a variable per block
+ *                      (64..65536, default 1024). */
+enum {
+    FBP_OPT_SPIN_LIMIT = 1, FBP_OPT_ENGINE_GRID = 2, FBP_OPT_ENGINE = 3, FBP_OPT_ENGINE_CLUSTER = 4,
+    FBP_OPT_FLOOD_HUB_MIN = 5, FBP_OPT_FLOOD_CHUNK = 6
+};
 int fbp_set_option(fbp_graph *g, int32_t option, int64_t value);
 
 /* Free the graph's device memory (after the stream's pending work). */

@@ -42,12 +42,15 @@ typedef struct {
 
 typedef struct fbp_batch fbp_batch;
 
-/* Per-part launch shapes (the autotuner's knobs): blocks of the level
- * engine (0 = automatic) and whether it runs as one thread-block cluster
- * (0 automatic, 1 never, 8 or 16 = cluster size). */
+/* Launch shapes (the autotuner's knobs): blocks of the level engine (0 =
+ * automatic), whether it runs as one thread-block cluster (0 automatic, 1
+ * never, 8 or 16 = cluster size), and the flooding split of long variable
+ * rows over blocks (FBP_OPT_FLOOD_HUB_MIN / FBP_OPT_FLOOD_CHUNK; 0 = default). */
 typedef struct {
     int32_t engine_grid;
     int32_t engine_cluster;
+    int32_t flood_hub_min;
+    int32_t flood_chunk;
 } fbp_batch_tuning;
 
 /* Build every graph on the device (copies all arrays; Algorithm 2 per graph

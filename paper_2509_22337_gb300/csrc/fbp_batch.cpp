@@ -70,7 +70,7 @@ struct fbp_batch {
     Part parts[kParts];
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr};
-    fbp_batch_tuning tuning{0, 0};
+    fbp_batch_tuning tuning{0, 0, 0, 0};
     fbp_stats stats{};
     float *scratch = nullptr;  // [largest union] marginals / pairs staging
     size_t scratch_n = 0;
@@ -441,11 +441,18 @@ extern "C" int fbp_batch_reset(fbp_batch *b)
 extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
 {
     if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
-    b->tuning = t ? *t : fbp_batch_tuning{0, 0};
-    if (b->tuning.engine_grid < 0 ||
-        (b->tuning.engine_cluster != 0 && b->tuning.engine_cluster != 1 && b->tuning.engine_cluster != 8 &&
-         b->tuning.engine_cluster != 16))
+    const fbp_batch_tuning v = t ? *t : fbp_batch_tuning{0, 0, 0, 0};
+    if (v.engine_grid < 0 ||
+        (v.engine_cluster != 0 && v.engine_cluster != 1 && v.engine_cluster != 8 && v.engine_cluster != 16))
         return fail(FBP_ERR_INVALID_ARG, "bad tuning");
+    Part &F = b->parts[kFlood];
+    if (F.g) {
+        int rc = fbp_set_option(F.g, FBP_OPT_FLOOD_HUB_MIN, v.flood_hub_min ? v.flood_hub_min : kFloodMediumMax);
+        if (!rc) rc = fbp_set_option(F.g, FBP_OPT_FLOOD_CHUNK, v.flood_chunk ? v.flood_chunk : kFloodHubChunk);
+        if (rc) return rc;
+        if (!F.g->flood_ready && (rc = build_flood_plan(F.g))) return rc;
+    }
+    b->tuning = v;
     return FBP_OK;
 }
 

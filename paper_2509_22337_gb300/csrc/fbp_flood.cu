@@ -515,9 +515,15 @@ void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float
 
 size_t flood_smem_bytes(int staged) { return (size_t)staged * (2 + kAccFloats) * sizeof(float); }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by every
+// graph: it only ever grows, so a graph never lowers it under another's launch.
 void flood_prepare(size_t smem_bytes)
 {
-    cudaFuncSetAttribute(k_a2v_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    static size_t current = 0;
+    if (smem_bytes > current) {
+        cudaFuncSetAttribute(k_a2v_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        current = smem_bytes;
+    }
 }
 
 }  // namespace fbp

@@ -70,6 +70,10 @@ struct fbp_graph {
     unsigned *h_res = nullptr;        // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     fbp_stats stats{};
+    // flooding split: rows longer than flood_hub_min run in chunks of
+    // flood_chunk entries (tunable; see FBP_OPT_FLOOD_*)
+    int flood_hub_min = fbp::kFloodMediumMax;
+    int flood_chunk = fbp::kFloodHubChunk;
     // batched union graphs: the batch member of every factor (empty for a
     // single graph); lane records carry it in bits 15.. of their packed word
     std::vector<int32_t> fac_graph;

@@ -218,6 +218,14 @@ int upload_erow(fbp_graph *g)
 int build_flood_plan(fbp_graph *g)
 {
     const HostCSR &h = g->h;
+    if (g->flood.small || g->flood.medium || g->flood.hub || g->flood.agg) {  // a rebuild after retuning
+        dfree(g, (void *)g->flood.small);
+        dfree(g, (void *)g->flood.medium);
+        dfree(g, (void *)g->flood.hub);
+        dfree(g, (void *)g->flood.hub_nchunks);
+        dfree(g, (void *)g->flood.agg);
+        g->flood = FloodPlanDev{};
+    }
     FloodPlanDev F;
     std::vector<int32_t> small, medium;
     std::vector<int4> hub;
@@ -229,14 +237,15 @@ int build_flood_plan(fbp_graph *g)
             small.push_back(v);
             continue;
         }
-        if (d <= kFloodMediumMax) {
+        if (d <= g->flood_hub_min) {
             medium.push_back(v);
             continue;
         }
+        const int32_t ch = g->flood_chunk;
         const int32_t c0 = (int32_t)hub.size();
-        const int32_t nc = (d + kFloodHubChunk - 1) / kFloodHubChunk;
+        const int32_t nc = (d + ch - 1) / ch;
         for (int32_t c = 0; c < nc; ++c) {
-            hub.push_back(make_int4(v, lo + c * kFloodHubChunk, std::min(hi, lo + (c + 1) * kFloodHubChunk), c0));
+            hub.push_back(make_int4(v, lo + c * ch, std::min(hi, lo + (c + 1) * ch), c0));
             hub_n.push_back(nc);
         }
     }
@@ -853,6 +862,17 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         return FBP_OK;
     case FBP_OPT_ENGINE:
         g->use_engine = value != 0;
+        return FBP_OK;
+    case FBP_OPT_FLOOD_HUB_MIN:
+        if (value < kFloodSmallMax || value > kFloodMediumMax)
+            return fail(FBP_ERR_INVALID_ARG, "hub threshold must be in [%d, %d]", kFloodSmallMax, kFloodMediumMax);
+        g->flood_hub_min = (int)value;
+        g->flood_ready = false;  // rebuilt at the next flooding run
+        return FBP_OK;
+    case FBP_OPT_FLOOD_CHUNK:
+        if (value < 64 || value > (1 << 16)) return fail(FBP_ERR_INVALID_ARG, "chunk must be in [64, 65536]");
+        g->flood_chunk = (int)value;
+        g->flood_ready = false;
         return FBP_OK;
     case FBP_OPT_ENGINE_CLUSTER:
         if (value != 0 && value != 1 && value != 8 && value != 16)

@@ -16,7 +16,8 @@ class fbp_graph_desc(C.Structure):
 
 
 class fbp_batch_tuning(C.Structure):
-    _fields_ = [("engine_grid", C.c_int32), ("engine_cluster", C.c_int32)]
+    _fields_ = [("engine_grid", C.c_int32), ("engine_cluster", C.c_int32), ("flood_hub_min", C.c_int32),
+                ("flood_chunk", C.c_int32)]
 
 
 def bind(L) -> None:
@@ -92,8 +93,8 @@ def fbp_batch_reset(b):
     return F._check(F.load().fbp_batch_reset(b))
 
 
-def fbp_batch_set_tuning(b, engine_grid=0, engine_cluster=0):
-    t = fbp_batch_tuning(int(engine_grid), int(engine_cluster))
+def fbp_batch_set_tuning(b, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0):
+    t = fbp_batch_tuning(int(engine_grid), int(engine_cluster), int(flood_hub_min), int(flood_chunk))
     return F._check(F.load().fbp_batch_set_tuning(b, C.addressof(t)))
 
 
@@ -128,8 +129,8 @@ class Batch:
     def reset(self):
         return fbp_batch_reset(self.h)
 
-    def tune(self, engine_grid=0, engine_cluster=0):
-        return fbp_batch_set_tuning(self.h, engine_grid, engine_cluster)
+    def tune(self, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0):
+        return fbp_batch_set_tuning(self.h, engine_grid, engine_cluster, flood_hub_min, flood_chunk)
 
     def stats(self):
         return fbp_batch_get_stats(self.h)

@@ -99,3 +99,17 @@ def test_batch_single_kind_and_empty_member(fbp):
     np.testing.assert_allclose(bt.marginals(1), [0.2, 0.5, 0.7, 0.5], atol=1e-7)
     assert iters[1] == 1
     bt.close()
+
+
+def test_many_graphs_of_different_sizes_interleaved(fbp):
+    """Graph handles of different sizes used in any order (kernel attributes
+    shared by all graphs must not be lowered by a smaller graph)."""
+    big = gen.bingo(n_tuples=20000, seed=31)
+    small = gen.bingo(n_tuples=300, seed=32)
+    A, Bh = fbp.Graph(big, "PARALL"), fbp.Graph(small, "PARALL")
+    A.run(2, 0.0)
+    Bh.run(2, 0.0)
+    A.run(2, 0.0)
+    Bh.run(2, 0.0)
+    A.close()
+    Bh.close()

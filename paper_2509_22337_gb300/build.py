@@ -18,7 +18,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfbp.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fbp_kernels.cu", "fbp_engine.cu", "fbp_flood.cu", "fbp_host.cpp", "fbp_sched.cpp", "fbp_batch.cpp", "fbp_serve.cpp"]
+SOURCES = ["fbp_kernels.cu", "fbp_engine.cu", "fbp_flood.cu", "fbp_host.cpp", "fbp_sched.cpp", "fbp_batch.cpp", "fbp_serve.cpp",
+           "fbp_fixed.cu"]
 
 
 def nvcc() -> str:
@@ -37,7 +38,7 @@ def _compile(src: str, extra: list[str] | None) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    deps.append(os.path.join(INCLUDE, "fbp.h"))
+    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc()] + _flags(extra) + ["-x", "cu" if src.endswith(".cu") else "c++", "-c", path, "-o", obj]

@@ -81,13 +81,14 @@ def load(path: str | None = None):
         L.fbp_get_stats.argtypes = [vp, C.POINTER(fbp_stats)]
         L.fbp_messages_reset.argtypes = [vp]
         L.fbp_set_option.argtypes = [vp, i32, i64]
+        L.fbp_run_fixed_scratch.argtypes = [vp, i32, f64, C.POINTER(i32), C.POINTER(f64)]
         L.fbp_graph_destroy.argtypes = [vp]
         L.fbp_graph_destroy.restype = None
         L.fbp_last_error.restype = C.c_char_p
         for name in ("fbp_graph_create", "fbp_schedule_set", "fbp_run", "fbp_marginals",
                      "fbp_schedule_levels", "fbp_schedule_build_host", "fbp_set_evidence",
                      "fbp_messages_export", "fbp_messages_import", "fbp_get_stats", "fbp_messages_reset",
-                     "fbp_set_option"):
+                     "fbp_set_option", "fbp_run_fixed_scratch"):
             getattr(L, name).restype = C.c_int
         _bind_extras(L)
         _lib = L
@@ -198,6 +199,19 @@ def fbp_run(g, max_iters: int, tol: float):
     return rc, it.value, res.value
 
 
+# include/fbp_fixed.h
+FBP_FIXED_SCRATCH_MAX_ITERS = 16384
+
+
+def fbp_run_fixed_scratch(g, max_iters: int, tol: float):
+    """fbp_run for a static strategy with no device allocation (per-run scratch
+    in the library's static device array; one call at a time per device).
+    Returns (status, iters, residual) like fbp_run."""
+    it, res = C.c_int32(), C.c_double()
+    rc = _check(load().fbp_run_fixed_scratch(g, int(max_iters), float(tol), C.byref(it), C.byref(res)))
+    return rc, it.value, res.value
+
+
 def fbp_marginals(g, n_vars: int, out=None):
     """Host numpy float32 [n_vars] (default) or into a CUDA torch tensor `out`."""
     if out is not None and hasattr(out, "data_ptr"):
@@ -286,6 +300,9 @@ class Graph:
 
     def run(self, max_iters: int, tol: float = 0.0):
         return fbp_run(self.h, max_iters, tol)
+
+    def run_fixed_scratch(self, max_iters: int, tol: float = 0.0):
+        return fbp_run_fixed_scratch(self.h, max_iters, tol)
 
     def marginals(self, out=None):
         return fbp_marginals(self.h, self.n_vars, out)

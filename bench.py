@@ -134,6 +134,35 @@ def algorithmic_bytes_flood(g):
     return 24 * E + 8 * V + 9 * A
 
 
+# Sources each profiled kernel is built from: a DRAM traffic figure taken by
+# ncu is reported only while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_engine": ["fbp_engine.cu", "fbp_msg.cuh", "fbp_internal.h"],
+    "flood": ["fbp_flood.cu", "fbp_flood.h", "fbp_msg.cuh", "fbp_internal.h"],
+}
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu summaries under profiles/, or None when there is none for
+    the kernel's current sources."""
+    import glob
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2509_22337_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    want = h.hexdigest()[:16]
+    pat = re.compile(r"traffic: (\S+) (\S+) dram_bytes_per_launch=(\d+) sources_sha256=([0-9a-f]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for m in pat.finditer(fh.read()):
+                if m.group(1) == kernel and m.group(2) == workload and m.group(4) == want:
+                    return int(m.group(3))
+    return None
+
+
 def run_batched(args, rank, world, local):
     """The batched workload: one fbp_batch run of 512 graphs vs a per-graph loop."""
     import torch
@@ -306,9 +335,11 @@ def run_gpu(args):
     per_launch_ms = kernel_ms / launches_per_step
     if strategy == "PARALL":
         kname = "k_v2a_flood + k_a2v_flood"
+        kkey = "flood"
         bytes_per_launch = algorithmic_bytes_flood(g) * sweeps / launches_per_step
     else:
         kname = "k_engine (persistent level engine, one launch per run)"
+        kkey = "k_engine"
         halves = 2 if strategy == "TOPO_FB" else 1
         bytes_per_launch = algorithmic_bytes_per_half(g) * halves * sweeps / launches_per_step
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -316,7 +347,7 @@ def run_gpu(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": kname,
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kkey, args.workload), "kernel": kname,
             "per_launch_us": round(per_launch_ms * 1e3, 3), "bytes_per_launch": int(bytes_per_launch),
             "peak_source": "measured" if os.path.exists(peaks_path) else "fallback"}
     levels_per_step = st["levels"] * sweeps

@@ -45,6 +45,10 @@ WORKLOADS = {
     "batched": ("batched", "MIXED", 0, 1e-6,
                 "512 graphs, sizes log-uniform in 1e3..1e5: even SmartFL-shaped (TOPO_FB, tol 1e-6, <= 100 "
                 "sweeps), odd BINGO-shaped (PARALL, tol 1e-6, <= 500 iterations); one batched run"),
+    "serving": ("serving", "PARALL", 500, 1e-6,
+                "64 resident BINGO-shaped sessions, 5e4..5e5 tuples (log-uniform); Poisson request stream "
+                "at 2000 req/s, each request clamps one unobserved tuple and re-runs PARALL warm to "
+                "max change < 1e-6 or 500 iterations; 120 GB HBM budget"),
 }
 
 
@@ -255,6 +259,126 @@ def run_batched(args, rank, world, local):
     B.close()
 
 
+def run_serving(args, rank, world, local):
+    """The served workload: resident sessions, an open-loop Poisson request
+    stream replayed at its own arrival times, continuous batching by the
+    library's server.  One step = one window of the stream (--serve-requests
+    arrivals); warm-up windows come from the stream after the timed ones."""
+    import threading
+    import torch
+    from paper_2509_22337_gb300 import fbp as F, fbp_serve as SV, gen
+
+    _, strategy, max_iters, tol, desc = WORKLOADS["serving"]
+    n_sess = args.serve_sessions
+    sessions = gen.serving_sessions(n_sess)
+    stream = gen.request_stream(sessions, 2000.0, 30.0)
+    per = args.serve_requests
+    need = per * (args.steps + args.warmup)
+    if need > len(stream):
+        raise SystemExit(f"the stream holds {len(stream)} requests, {need} asked for")
+    srv = SV.Server(hbm_budget_bytes=120 << 30, max_inflight=args.serve_inflight,
+                    iters_per_tick=args.serve_tick)
+    t0 = time.perf_counter()
+    sids = [srv.open(g, strategy, max_iters, tol) for g in sessions]
+    while srv.stats()["sessions_warming"] > 0:
+        time.sleep(0.01)
+    load_s = time.perf_counter() - t0
+
+    def replay(window):
+        """Submit each request at its arrival time (relative to the window's
+        first), wait for all; returns (infos, wall seconds)."""
+        base = float(window["t"][0])
+        tickets = []
+        start = time.perf_counter()
+        for r in window:
+            delay = (float(r["t"]) - base) - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(sids[int(r["session"])], int(r["var"]), int(r["value"])))
+        infos = [srv.wait(t)[0] for t in tickets]
+        return infos, time.perf_counter() - start
+
+    for w in range(args.warmup):  # warm-up windows: the end of the stream
+        replay(stream[len(stream) - per * (w + 1): len(stream) - per * w])
+    infos, wall = [], 0.0
+    st0 = srv.stats()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            i, dt = replay(stream[k * per:(k + 1) * per])
+            infos += i
+            wall += dt
+    st1 = srv.stats()
+    lat = np.array([i["latency_ms"] for i in infos])
+    svc = np.array([i["latency_ms"] - i["queue_ms"] for i in infos])
+    dev = np.array([i["device_ms"] for i in infos])
+    its = np.array([i["iters"] for i in infos])
+    assert all(i["state"] == SV.FBP_REQ_DONE for i in infos), "a served request failed"
+    value = len(infos) / wall
+    # algorithmic bytes of every iteration the timed requests ran
+    sess_bytes = [algorithmic_bytes_flood(g) for g in sessions]
+    moved = sum(sess_bytes[i["session"]] * i["iters"] for i in infos)
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    achieved = moved / wall / 1e9
+    srv.close()
+
+    # cold-start per-request plain path on a sample of the same requests: a new
+    # graph with the session's evidence so far, a run from uniform messages,
+    # marginals to the host
+    cold = []
+    evid = [np.array(g.evidence, copy=True) for g in sessions]
+    for r in stream[: per * args.steps]:
+        evid[int(r["session"])][int(r["var"])] = int(r["value"])
+        if len(cold) >= args.cold_sample:
+            continue
+        g = sessions[int(r["session"])]
+        gc = gen.FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, g.factor_type, g.factor_param, g.prior_p1,
+                             evid[int(r["session"])].copy(), g.name)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        G = F.Graph(gc, strategy)
+        G.run(max_iters, tol)
+        G.marginals()
+        G.close()
+        torch.cuda.synchronize()
+        cold.append((time.perf_counter() - t1) * 1e3)
+    cold = np.array(cold)
+    n_vars_mean = float(np.mean([sessions[i["session"]].n_vars for i in infos]))
+    line = {
+        "metric": "served requests/s", "value": round(value, 2), "unit": "req/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "desc": desc, "n_sessions": n_sess,
+                   "n_vars": int(sum(g.n_vars for g in sessions)), "n_edges": int(sum(g.n_edges for g in sessions)),
+                   "requests_per_step": per, "offered_rate_req_s": 2000.0, "max_inflight": args.serve_inflight,
+                   "iters_per_tick": args.serve_tick, "hbm_budget_gb": 120,
+                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
+                       "note": "submission to result on the host, queueing under the offered rate included"},
+        "service_ms": {"p50": round(float(np.percentile(svc, 50)), 3), "p99": round(float(np.percentile(svc, 99)), 3)},
+        "device_ms": {"p50": round(float(np.percentile(dev, 50)), 3), "p99": round(float(np.percentile(dev, 99)), 3)},
+        "iters_per_request": {"mean": round(float(its.mean()), 1), "max": int(its.max())},
+        "load_s": round(load_s, 2),
+        "cold_start": {"req_per_s": round(1e3 / float(cold.mean()), 3),
+                       "service_ms_p50": round(float(np.percentile(cold, 50)), 3),
+                       "service_ms_max": round(float(cold.max()), 3), "sample": len(cold),
+                       "what": "per request: fbp_graph_create with the evidence so far, fbp_run from uniform "
+                               "messages, marginals to the host, destroy; one request at a time"},
+        "speedup_vs_cold": round(value / (1e3 / float(cold.mean())), 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "flooding iteration kernels of all running requests (24E+8V+9A per iteration)"},
+        "e2e": {"value": round(value, 2), "unit": "req/s", "h2d_bytes_per_step": 4 * per,
+                "d2h_bytes_per_step": int(4 * n_vars_mean * per),
+                "note": "each request is submitted from the host and its marginals land in host memory"},
+        "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "server": {"ticks": int(st1["ticks"] - st0["ticks"]), "peak_inflight": st1["peak_inflight"],
+                   "resident_gb": round(st1["peak_resident_bytes"] / 2**30, 2)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def run_gpu(args):
     import torch
 
@@ -271,8 +395,8 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     F.load()
-    if args.workload == "batched":
-        run_batched(args, rank, world, local)
+    if args.workload in ("batched", "serving"):
+        (run_batched if args.workload == "batched" else run_serving)(args, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -471,6 +595,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=512)
+    ap.add_argument("--serve-sessions", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--serve-inflight", type=int, default=64)
+    ap.add_argument("--serve-tick", type=int, default=16)
+    ap.add_argument("--cold-sample", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -13,7 +13,7 @@
  * at its own max_iters), exactly as a single-graph fbp_run would, so results
  * equal the per-graph runs.
  *
- * Served form: see the fbp_server_* entry points below.
+ * Served form: include/fbp_serve.h.
  */
 #ifndef FBP_BATCH_H
 #define FBP_BATCH_H

@@ -39,9 +39,10 @@ namespace fbp {
 
 namespace {
 
-constexpr int kBlock = 256;    // threads per block
+constexpr int kBlock = 256;    // threads per block (grid mode)
+constexpr int kClusterBlock = 512;  // threads per block in cluster mode: 16 x 16 warps hold a level
 constexpr int kMaxFan = 32;    // largest factor held by one warp (larger: per-edge path)
-constexpr int kPre = 8;        // row entries of a lane prefetched into registers
+constexpr int kPre = 16;       // row entries of a lane prefetched into registers
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
@@ -124,17 +125,33 @@ struct Pre {
     int kmore, kend;   // rest of the row
 };
 
-__device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
-                                         int s1)
+// The lane record and row range of a slot: the first of the two dependent
+// rounds of a lane's read-only loads.
+struct PreA {
+    int4 rec;
+    int2 er;
+};
+
+__device__ __forceinline__ void prefetch_a(PreA &a, const LevelPlanDev &P, int slot, int s1)
 {
-    s.rec = make_int4(-1, 0, 0, 0);
+    a.rec = make_int4(-1, 0, 0, 0);
+    a.er = make_int2(0, 0);
+    if (slot >= s1) return;
+    a.rec = __ldg(P.lanes + slot);
+    a.er = __ldg(P.lrow + slot);  // independent of rec: both loads in flight together
+}
+
+// The second round (unary potential and the first row entries), from a
+// completed first round.
+__device__ __forceinline__ void prefetch_b(Pre &s, const PreA &a, const EngineArgs &A, const LevelPlanDev &P,
+                                           int La)
+{
+    s.rec = a.rec;
     s.use_nxt = 0u;
     s.live = 0u;
     s.kmore = s.kend = 0;
     s.phi = 1.f;
-    if (slot >= s1) return;
-    s.rec = __ldg(P.lanes + slot);
-    const int2 er = __ldg(P.lrow + slot);  // independent of rec: both loads in flight together
+    const int2 er = a.er;
     const int q = s.rec.x;
     if (q < 0) return;
     s.phi = __ldg(A.g.phi + s.rec.w);
@@ -151,6 +168,14 @@ __device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const Leve
     }
     s.kmore = er.x + kPre;
     s.kend = er.y;
+}
+
+__device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
+                                         int s1)
+{
+    PreA a;
+    prefetch_a(a, P, slot, s1);
+    prefetch_b(s, a, A, P, La);
 }
 
 // One lane's share of a level: its position's v->a product, then (if its edge
@@ -259,10 +284,10 @@ __device__ __forceinline__ LevelPlanDev plan_at(const EngineArgs &A, int h)
     return h == 0 ? A.half[0] : A.half[1];
 }
 
-template <bool kCluster>
-__global__ void __launch_bounds__(kBlock, 1) k_engine(EngineArgs A)
+template <bool kCluster, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
 {
-    __shared__ P2 s_m[kBlock];
+    __shared__ P2 s_m[kThreads];
     P2 *sm = s_m + (threadIdx.x & ~31);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     // A level's warp groups are dealt to warps round-robin over the blocks, so
@@ -292,6 +317,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine(EngineArgs A)
             for (int L = 0; L < P.n_levels; ++L) {
                 const int La = L + P.level_base;
                 const int s0 = __ldg(P.lane_ptr + L), s1 = __ldg(P.lane_ptr + L + 1);
+                // the next level (next half, or the next iteration's first
+                // level): its lane records are requested before this level's
+                // work and its dependent loads between the barrier's arrive and
+                // wait, so that neither round trip adds to the level's time
+                int Ln = L + 1, hn = h;
+                LevelPlanDev Pn = P;
+                while (Ln >= Pn.n_levels) {
+                    Ln = 0;
+                    hn = hn + 1 < A.n_halves ? hn + 1 : 0;
+                    Pn = plan_at(A, hn);
+                    if (Pn.n_levels > 0) break;
+                }
+                PreA next;
+                prefetch_a(next, Pn, __ldg(Pn.lane_ptr + Ln) + my0, __ldg(Pn.lane_ptr + Ln + 1));
                 run_lane(pre, A, P, La, cur, nxt, sm, rmax, ng);
                 for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
                     Pre more;
@@ -324,18 +363,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine(EngineArgs A)
                     grid_arrive(A.bar);
                     target += gridDim.x;
                 }
-                {   // the next level (next half, or the next iteration's first level)
-                    int Ln = L + 1, hn = h;
-                    LevelPlanDev Pn = P;
-                    while (Ln >= Pn.n_levels) {
-                        Ln = 0;
-                        hn = hn + 1 < A.n_halves ? hn + 1 : 0;
-                        Pn = plan_at(A, hn);
-                        if (Pn.n_levels > 0) break;
-                    }
-                    prefetch(pre, A, Pn, Ln + Pn.level_base, __ldg(Pn.lane_ptr + Ln) + my0,
-                             __ldg(Pn.lane_ptr + Ln + 1));
-                }
+                // the dependent round uses its loads at once: inside the barrier
+                prefetch_b(pre, next, A, Pn, Ln + Pn.level_base);
                 if (kCluster) {
                     cluster_wait();
                 } else if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
@@ -394,7 +423,7 @@ int engine_max_grid()
     static int cap = 0;
     if (!cap) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine<false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine<false, kBlock>, kBlock, 0);
         cap = per_sm * num_sms();
         if (cap < 1) cap = 1;
     }
@@ -408,11 +437,11 @@ int engine_cluster_size()
     static int size = -1;
     if (size < 0) {
         size = 0;
-        cudaFuncSetAttribute(k_engine<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_engine<true, kClusterBlock>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(c);
-            cfg.blockDim = dim3(kBlock);
+            cfg.blockDim = dim3(kClusterBlock);
             cudaLaunchAttribute attr;
             attr.id = cudaLaunchAttributeClusterDimension;
             attr.val.clusterDim.x = c;
@@ -421,7 +450,7 @@ int engine_cluster_size()
             cfg.attrs = &attr;
             cfg.numAttrs = 1;
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k_engine<true>, &cfg) == cudaSuccess && n > 0) {
+            if (cudaOccupancyMaxActiveClusters(&n, k_engine<true, kClusterBlock>, &cfg) == cudaSuccess && n > 0) {
                 size = c;
                 break;
             }
@@ -437,7 +466,7 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
     if (cluster > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cluster);
-        cfg.blockDim = dim3(kBlock);
+        cfg.blockDim = dim3(kClusterBlock);
         cfg.stream = s;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
@@ -446,13 +475,13 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
         attr.val.clusterDim.z = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_engine<true>, args);
+        return cudaLaunchKernelEx(&cfg, k_engine<true, kClusterBlock>, args);
     }
     const int cap = engine_max_grid();
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     void *params[] = {&args};
-    return cudaLaunchCooperativeKernel((void *)k_engine<false>, dim3(grid), dim3(kBlock), params, 0, s);
+    return cudaLaunchCooperativeKernel((void *)k_engine<false, kBlock>, dim3(grid), dim3(kBlock), params, 0, s);
 }
 
 }  // namespace fbp

@@ -296,3 +296,22 @@ def test_barrier_timeout_is_reported_and_context_survives(fbp):
     G.close()
     ref = gpu_run(fbp, g, "TOPO_FB", 3, 0.0)
     assert np.array_equal(p.astype(np.float64), ref["p"])
+
+
+@pytest.mark.parametrize("cluster", [8, 16])
+def test_engine_cluster_mode_does_not_change_results(fbp, cluster):
+    """One thread-block cluster with the hardware barrier runs the same
+    arithmetic as the cooperative grid, also when a level is wider than the
+    cluster holds (several passes per level)."""
+    for g in (gen.smartfl(n_layers=15, width=60, seed=62), gen.smartfl(n_layers=5, width=4000, seed=64)):
+        G = fbp.Graph(g, "TOPO_FB")
+        G.set_option(fbp.FBP_OPT_ENGINE_GRID, 152)
+        G.run(4, 0.0)
+        a = G.messages()
+        G.close()
+        H = fbp.Graph(g, "TOPO_FB")
+        H.set_option(fbp.FBP_OPT_ENGINE_CLUSTER, cluster)
+        H.run(4, 0.0)
+        b = H.messages()
+        H.close()
+        assert np.array_equal(a, b), (g.name, cluster)

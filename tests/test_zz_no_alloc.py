@@ -43,17 +43,25 @@ def test_allocates_nothing_where_fbp_run_would(fbp):
     """A fresh graph's residual words cover 64 iterations; fbp_run grows them
     through the graph's allocator (PyTorch's caching allocator here) for a
     longer run, the fixed-scratch call must not touch the allocator."""
+    import gc
     import torch
     fg = gen.smartfl(n_layers=16, width=80, seed=62, planted=True)
     a, b = fbp.Graph(fg, "TOPO_FB"), fbp.Graph(fg, "TOPO_FB")
-    torch.cuda.synchronize()
-    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
-    rb = b.run_fixed_scratch(3000, 0.0)
-    rb2 = b.run_fixed_scratch(3000, 0.0)
-    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
-    assert before == after
-    ra = a.run(3000, 0.0)
-    assert torch.cuda.memory_allocated() > before[0]  # fbp_run did grow its residual words
+    # graphs left by earlier tests free their memory when collected: collect
+    # them now and keep the collector off while the allocator is watched
+    gc.collect()
+    gc.disable()
+    try:
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+        rb = b.run_fixed_scratch(3000, 0.0)
+        rb2 = b.run_fixed_scratch(3000, 0.0)
+        after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+        assert before == after
+        ra = a.run(3000, 0.0)
+        assert torch.cuda.memory_allocated() > before[0]  # fbp_run did grow its residual words
+    finally:
+        gc.enable()
     ra2 = a.run(3000, 0.0)
     _same(a, b, ra2, rb2, "second 3000-iteration call")
     assert ra[1] == rb[1] == 3000

@@ -233,22 +233,29 @@ int run_flood(fbp_batch *b, Part &P)
     F.vgraph = P.vgraph;
     F.fgraph = P.fgraph;
     F.batch = P.ctl();
-    IterCtl ctl{g->d_res, g->d_guards};
-    int32_t next = 1, batch = 4;
-    bool done = false;
-    while (next <= P.max_iters && !done) {
-        const int32_t last = std::min(P.max_iters, next + batch - 1);
-        for (int32_t it = next; it <= last; ++it) {
-            flood_iteration(g->d, F, g->a2v[g->cur], g->v2a, ctl, g->flood_staged, it, 0.f, g->d_res_it, g->d_out,
-                            g->stream);
-            b->stats.kernel_launches += 5;
+    // captured chunks of iterations, replayed in growing batches; the device
+    // counts iterations and stops each member at its own rule
+    if (P.max_iters == 0) return FBP_OK;
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = flood_exec_for(g, F, 0.f, kFloodChunk, &exec))) return rc;
+    g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
+    g->h_out[3] = P.max_iters;
+    e = cudaMemcpyAsync(g->d_out, g->h_out, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "flood batch: %s", cudaGetErrorString(e));
+    const int per_iter = flood_launches(g->d, F);
+    int32_t queued = 0, reps = 1;
+    while (queued < P.max_iters) {
+        for (int32_t r = 0; r < reps && queued < P.max_iters; ++r) {
+            e = cudaGraphLaunch(exec, g->stream);
+            if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "flood batch: %s", cudaGetErrorString(e));
+            queued += kFloodChunk;
+            b->stats.kernel_launches += (int64_t)kFloodChunk * per_iter;
         }
         e = cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
         if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "flood batch: %s", cudaGetErrorString(e));
-        done = g->h_out[0] != 0;
-        next = last + 1;
-        batch = std::min(batch * 2, 64);
+        if (g->h_out[0] != 0) break;
+        reps = std::min(reps * 2, 8);
     }
     return FBP_OK;
 }

@@ -16,9 +16,9 @@
 //   rows of degree <= 256     one warp per row
 //   longer rows (hubs)        chunks of kFloodHubChunk entries, one block each; a
 //                             pre-pass writes each chunk's partial product
-// Phase 2, the closed-form local-structure messages: one thread per factor,
-// the block's factor rows staged through shared memory so that the v->a reads
-// and the a->v read-modify-write are coalesced.
+// Phase 2, the closed-form local-structure messages: one lane per message,
+// whole factors per warp, the factor's other messages by warp shuffle;
+// factors wider than a warp one thread per edge.
 #include "fbp_msg.cuh"
 #include "fbp_flood.h"
 
@@ -296,159 +296,132 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
 // ----------------------------------------------------------------------------
 // Phase 2
 // ----------------------------------------------------------------------------
-// Accumulators of the closed forms over a run of premises (fbp_msg.cuh):
-// P1, P0, Ps and the first-false sums D, D0.  Runs concatenate exactly:
-//   P(A.B) = P(A) P(B),  D(A.B) = D(A) Ps(B) + P1(A) D(B),
-//   D0(A.B) = D0(A) Ps(B) + P0(A) D0(B),
-// which gives every target's "all premises but one" accumulators from one
-// forward (prefix) and one backward (suffix) pass: O(n) per factor.
-struct Acc {
-    float P1, P0, Ps, D, D0;
-};
-
-__device__ __forceinline__ Acc acc_one() { return Acc{1.f, 1.f, 1.f, 0.f, 0.f}; }
-
-__device__ __forceinline__ Acc acc_append(const Acc &a, P2 m)  // A . {m}
+// Per-graph residual of a batch: one atomic per graph present in the warp.
+__device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph, float d)
 {
-    const float s = m.m0 + m.m1;
-    return Acc{a.P1 * m.m1, a.P0 * m.m0, a.Ps * s, fmaf(a.D, s, a.P1 * m.m0), fmaf(a.D0, s, a.P0 * m.m1)};
+    const unsigned grp = __match_any_sync(0xffffffffu, graph);
+    const unsigned bits = __reduce_max_sync(grp, __float_as_uint(d));
+    if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) atomicMax(F.batch.res + graph, bits);
 }
 
-__device__ __forceinline__ Acc acc_prepend(P2 m, const Acc &b)  // {m} . B
-{
-    const float s = m.m0 + m.m1;
-    return Acc{m.m1 * b.P1, m.m0 * b.P0, s * b.Ps, fmaf(m.m0, b.Ps, m.m1 * b.D), fmaf(m.m1, b.Ps, m.m0 * b.D0)};
-}
-
-__device__ __forceinline__ Acc acc_concat(const Acc &a, const Acc &b)
-{
-    return Acc{a.P1 * b.P1, a.P0 * b.P0, a.Ps * b.Ps, fmaf(a.D, b.Ps, a.P1 * b.D), fmaf(a.D0, b.Ps, a.P0 * b.D0)};
-}
-
-constexpr int kAccFloats = 5;
-constexpr int kLinearMaxFan = 64;  // wider factors use the per-target loop
-
-// Phase 2 for one factor, O(n): outputs replace the old values in io.
-__device__ __forceinline__ void factor_linear(int type, float p, int n, const float *in, float *io, float *pre,
-                                              int stride, float &rmax, unsigned long long &ng)
-{
-    const unsigned t = 1u << type;
-    constexpr unsigned AND = 1u << kTypeAND, OR = 1u << kTypeOR, NOT = 1u << kTypeNOT, EQ = 1u << kTypeEQ,
-                       NI = 1u << kTypeNOISY_IMPLY, NA = 1u << kTypeNOISY_AND, PR = 1u << kTypePRIOR;
-    const float q = 1.f - p;
-    const int y = n - 1;
-    Acc acc = acc_one();
-    for (int j = 0; j < y; ++j) {
-        pre[j] = acc.P1;
-        pre[stride + j] = acc.P0;
-        pre[2 * stride + j] = acc.Ps;
-        pre[3 * stride + j] = acc.D;
-        pre[4 * stride + j] = acc.D0;
-        acc = acc_append(acc, dec(in[j]));
-    }
-    {   // the output (or only) variable
-        const float a0 = (t & NOT) ? 1.f : (t & (NA | NI | PR)) ? q : 0.f;
-        const float a1 = (t & (AND | NA | NI)) ? 1.f : 0.f;
-        const float a2 = (t & (OR | EQ)) ? 1.f : 0.f;
-        const float b0 = (t & (AND | EQ)) ? 1.f : (t & (NA | NI | PR)) ? p : 0.f;
-        const float b1 = (t & NI) ? 1.f : 0.f;
-        const float b2 = (t & OR) ? 1.f : 0.f;
-        const float b3 = (t & NOT) ? 1.f : 0.f;
-        const P2 mu{fmaf(a0, acc.P1, fmaf(a1, acc.D, a2 * acc.P0)),
-                    fmaf(b0, acc.P1, fmaf(b1, acc.D, fmaf(b2, acc.D0, b3 * acc.P0)))};
-        bool gd = false;
-        const float r = enc_fast(mu, gd);
-        ng += gd;
-        rmax = fmaxf(rmax, delta_p1_fast(r, io[y]));
-        io[y] = r;
-    }
-    if (y == 0) return;
-    const P2 my = dec(in[y]);
-    const float sy = my.m0 + my.m1, w = fmaf(p, my.m1, q * my.m0);
-    const float c0 = (t & (AND | NA)) ? my.m0 : (t & NOT) ? my.m1 : (t & NI) ? sy : 0.f;
-    const float c1 = (t & (OR | EQ)) ? my.m0 : 0.f;
-    const float c2 = (t & OR) ? my.m1 : 0.f;
-    const float d0 = (t & (AND | EQ)) ? my.m1 : (t & (NA | NI)) ? w : 0.f;
-    const float d1 = (t & (AND | NA)) ? my.m0 : (t & NI) ? sy : 0.f;
-    const float d2 = (t & OR) ? my.m1 : (t & NOT) ? my.m0 : 0.f;
-    Acc suf = acc_one();
-    for (int j = y - 1; j >= 0; --j) {
-        const Acc pr{pre[j], pre[stride + j], pre[2 * stride + j], pre[3 * stride + j], pre[4 * stride + j]};
-        const Acc ex = acc_concat(pr, suf);
-        const P2 mu{fmaf(c0, ex.Ps, fmaf(c1, ex.P0, c2 * ex.D0)), fmaf(d0, ex.P1, fmaf(d1, ex.D, d2 * ex.Ps))};
-        bool gd = false;
-        const float r = enc_fast(mu, gd);
-        ng += gd;
-        const float mj = in[j];
-        rmax = fmaxf(rmax, delta_p1_fast(r, io[j]));
-        io[j] = r;
-        suf = acc_prepend(dec(mj), suf);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_a2v_rows(const DevGraph g, const FloodPlanDev F,
-                                                  const float *__restrict__ v2a, float *__restrict__ a2v,
-                                                  IterCtl ctl, int staged)
+// One lane per message: each warp holds whole factors (consecutive in the
+// factor-major order, so its edges are one contiguous range and every load
+// and the store are coalesced).  A lane reads its own incoming v->a message;
+// the factor's other messages come from the neighbouring lanes by shuffle, in
+// premise order (the order of a2v_unified, so the arithmetic is the level
+// engine's), over a trip count that is uniform in the warp, so that factors of
+// different types and fan-ins in one warp run one instruction stream.  A
+// factor of at most 32 variables has Ps <= 2^31, so the products need no
+// rescaling here.  The a->v messages are written in place: phase 2 reads only
+// v->a messages.
+__global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const FloodPlanDev F,
+                                                   const float *__restrict__ v2a, float *__restrict__ a2v, IterCtl ctl)
 {
     if (*(volatile const int *)F.done) return;
-    extern __shared__ float s_dyn[];
-    const int a0 = blockIdx.x * blockDim.x, a1 = min(a0 + (int)blockDim.x, g.na);
-    const int e0 = __ldg(g.fptr + a0), e1 = __ldg(g.fptr + a1);
-    const int cnt = e1 - e0;
-    float *s_in = s_dyn, *s_io = s_dyn + staged, *s_pre = s_dyn + 2 * staged;
-    const bool st = cnt <= staged;  // block-uniform
-    if (st) {
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            s_in[i] = __ldg(v2a + e0 + i);
-            s_io[i] = a2v[e0 + i];
-        }
-        __syncthreads();
-    }
-    float rmax = 0.f;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    float d = 0.f;
     unsigned long long ng = 0;
-    const int a = a0 + threadIdx.x;
-    const int graph = (F.batch.n_graphs > 0 && a < a1) ? __ldg(F.fgraph + a) : -1;
-    const bool frozen = graph >= 0 && __ldcg(F.batch.done + graph) != 0;
-    if (a < a1 && !frozen) {
-        const int lo = __ldg(g.fptr + a), n = __ldg(g.fptr + a + 1) - lo;
-        const int type = __ldg(g.ftype + a);
-        const float p = __ldg(g.fparam + a);
-        if (st && n <= kLinearMaxFan) {
-            factor_linear(type, p, n, s_in + (lo - e0), s_io + (lo - e0), s_pre + (lo - e0), staged, rmax, ng);
-        } else {
-            // unstaged block or very wide factor: per-target closed forms
-            const float *in = st ? s_in + (lo - e0) : v2a + lo;
-            float *io = st ? s_io + (lo - e0) : a2v + lo;
-            for (int i = 0; i < n; ++i) {
-                bool gd = false;
-                const float r = enc_fast(a2v_unified(type, p, n, i, [&](int j) { return dec(in[j]); }), gd);
-                ng += gd;
-                rmax = fmaxf(rmax, delta_p1_fast(r, io[i]));
-                io[i] = r;
+    int graph = -1;
+    if (w < F.n_warps) {  // warp-uniform
+        const int4 wr = __ldg(F.warps + w);  // {first edge, end edge, first factor, end factor}
+        const int e = wr.x + lane;
+        const bool valid = e < wr.y;
+        int lo = wr.x, n = 1, type = 0;
+        float p = 0.f, x = 1.f, old = 1.f;
+        bool frozen = false;
+        if (valid) {
+            const int a = __ldg(g.efac + e);
+            lo = __ldg(g.fptr + a);
+            n = __ldg(g.fptr + a + 1) - lo;
+            type = __ldg(g.ftype + a);
+            p = __ldg(g.fparam + a);
+            x = __ldg(v2a + e);
+            old = a2v[e];
+            if (F.batch.n_graphs > 0) {
+                graph = __ldg(F.fgraph + a);
+                frozen = __ldcg(F.batch.done + graph) != 0;
             }
         }
-    }
-    if (st) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) a2v[e0 + i] = s_io[i];
+        const int first = lo - wr.x, i = e - lo, y = n - 1;
+        const int span = __reduce_max_sync(0xffffffffu, valid ? y : 0);
+        Acc5 A;
+        for (int j = 0; j < span; ++j) {
+            const float r = __shfl_sync(0xffffffffu, x, (first + j) & 31);
+            if (j < y && j != i) {
+                const P2 m = dec(r);
+                const float s = m.m0 + m.m1;
+                A.D = fmaf(A.D, s, A.P1 * m.m0);
+                A.D0 = fmaf(A.D0, s, A.P0 * m.m1);
+                A.P1 *= m.m1;
+                A.P0 *= m.m0;
+                A.Ps *= s;
+            }
+        }
+        const float ry = __shfl_sync(0xffffffffu, x, (first + y) & 31);
+        if (valid && !frozen) {
+            const P2 mu = a2v_finish(type, p, i == y, A, dec(ry));
+            bool gd = false;
+            const float r = enc_fast(mu, gd);
+            ng += gd;
+            d = delta_p1_fast(r, old);
+            a2v[e] = r;
+        }
     }
     if (ng) atomicAdd(ctl.guards, ng);
     if (F.batch.n_graphs > 0) {
-        // per-graph residual: one atomic per graph present in the warp
-        const unsigned grp = __match_any_sync(0xffffffffu, graph);
-        const unsigned bits = __reduce_max_sync(grp, __float_as_uint(rmax));
-        if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) atomicMax(F.batch.res + graph, bits);
+        batch_residual(F, graph, d);
         return;
     }
-    const float bm = block_max(rmax);
+    const float bm = block_max(d);
+    if (threadIdx.x == 0 && bm > 0.f) atomicMax(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
+}
+
+// Factors wider than a warp: one thread per edge, the closed form over the
+// factor's v->a messages read from memory.
+__global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodPlanDev F,
+                                                  const float *__restrict__ v2a, float *__restrict__ a2v, IterCtl ctl)
+{
+    if (*(volatile const int *)F.done) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.f;
+    unsigned long long ng = 0;
+    int graph = -1;
+    if (k < F.n_wide) {
+        const int e = __ldg(F.wide + k);
+        const int a = __ldg(g.efac + e);
+        const int lo = __ldg(g.fptr + a), n = __ldg(g.fptr + a + 1) - lo;
+        bool frozen = false;
+        if (F.batch.n_graphs > 0) {
+            graph = __ldg(F.fgraph + a);
+            frozen = __ldcg(F.batch.done + graph) != 0;
+        }
+        if (!frozen) {
+            const P2 mu = a2v_unified(__ldg(g.ftype + a), __ldg(g.fparam + a), n, e - lo,
+                                      [&](int j) { return dec(__ldg(v2a + lo + j)); });
+            bool gd = false;
+            const float r = enc_fast(mu, gd);
+            ng += gd;
+            d = delta_p1_fast(r, a2v[e]);
+            a2v[e] = r;
+        }
+    }
+    if (ng) atomicAdd(ctl.guards, ng);
+    if (F.batch.n_graphs > 0) {
+        batch_residual(F, graph, d);
+        return;
+    }
+    const float bm = block_max(d);
     if (threadIdx.x == 0 && bm > 0.f) atomicMax(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
 // End of an iteration of a batch: per-graph bookkeeping as in the persistent
-// engine; the run is done when no graph is running.
-__global__ void k_flood_batch_check(BatchCtl B, int it, int *ctl)
+// engine; the run is done when no graph is running.  The iteration number is
+// the device's own count (ctl[1] + 1), so a captured chunk of iterations can
+// be replayed.
+__global__ void k_flood_batch_check(BatchCtl B, int *ctl)
 {
     if (*(volatile int *)ctl) return;
+    const int it = ctl[1] + 1;
     __shared__ int s_active;
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
@@ -468,17 +441,19 @@ __global__ void k_flood_batch_check(BatchCtl B, int it, int *ctl)
     __syncthreads();
     if (threadIdx.x == 0) {
         ctl[1] = it;
-        if (s_active == 0) ctl[0] = 1;
+        if (s_active == 0 || it >= ctl[3]) ctl[0] = 1;
     }
 }
 
-// End of an iteration: the residual of iteration `it` is the max over the
-// slots; the slots are cleared for the next iteration; the run is marked done
-// at the first iteration below tol.  Later iterations of the same batch see
-// the flag and return at once.
-__global__ void k_flood_check(unsigned *slots, unsigned *hist, int it, float tol, int *ctl)
+// End of an iteration: the residual of iteration it = ctl[1] + 1 is the max
+// over the slots; the slots are cleared for the next iteration; the run is
+// marked done (ctl[0] = 1) at the first iteration below tol, or (ctl[0] = 2)
+// at the iteration limit ctl[3].  Later iterations see the flag and return at
+// once.
+__global__ void k_flood_check(unsigned *slots, unsigned *hist, float tol, int *ctl)
 {
     if (*(volatile int *)ctl) return;
+    const int it = ctl[1] + 1;
     const unsigned v = threadIdx.x < kResSlots ? slots[threadIdx.x] : 0u;
     const unsigned m = __reduce_max_sync(0xffffffffu, v);
     __shared__ unsigned s_m[kResSlots / 32];
@@ -491,13 +466,14 @@ __global__ void k_flood_check(unsigned *slots, unsigned *hist, int it, float tol
         hist[it - 1] = r;
         ctl[1] = it;
         if (__uint_as_float(r) < tol) ctl[0] = 1;
+        else if (it >= ctl[3]) ctl[0] = 2;
     }
 }
 
 }  // namespace
 
-void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl,
-                     int staged, int it, float tol, unsigned *hist, int *done, cudaStream_t s)
+void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+                     unsigned *hist, int *done, cudaStream_t s)
 {
     FloodPlanDev P = F;
     P.done = done;
@@ -505,25 +481,36 @@ void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float
     if (P.n_hub > 0) k_hub_partials<<<P.n_hub, 256, 0, s>>>(g, P, a2v);
     const int nb = P.nb_small + P.nb_medium + P.n_hub;
     if (nb > 0) k_v2a_rest<<<nb, 256, 0, s>>>(g, P, a2v, v2a);
-    if (g.na > 0) {
-        const int blocks = (g.na + 255) / 256;
-        k_a2v_rows<<<blocks, 256, flood_smem_bytes(staged), s>>>(g, P, v2a, a2v, ctl, staged);
-    }
-    if (P.batch.n_graphs > 0) k_flood_batch_check<<<1, 1024, 0, s>>>(P.batch, it, done);
-    else k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, it, tol, done);
+    if (P.n_warps > 0) k_a2v_lanes<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+    if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+    if (P.batch.n_graphs > 0) k_flood_batch_check<<<1, 1024, 0, s>>>(P.batch, done);
+    else k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, tol, done);
 }
 
-size_t flood_smem_bytes(int staged) { return (size_t)staged * (2 + kAccFloats) * sizeof(float); }
-
-// The dynamic shared-memory limit is a property of the kernel, shared by every
-// graph: it only ever grows, so a graph never lowers it under another's launch.
-void flood_prepare(size_t smem_bytes)
+cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+                          unsigned *hist, int *done, int iters, cudaGraphExec_t *exec)
 {
-    static size_t current = 0;
-    if (smem_bytes > current) {
-        cudaFuncSetAttribute(k_a2v_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-        current = smem_bytes;
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < iters; ++k) flood_iteration(g, F, a2v, v2a, ctl, tol, hist, done, cap);
+        const cudaError_t launch = cudaGetLastError();
+        e = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess && launch != cudaSuccess) e = launch;
     }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    return e;
+}
+
+int flood_launches(const DevGraph &g, const FloodPlanDev &F)
+{
+    return (g.nv > 0) + (F.n_hub > 0) + (F.nb_small + F.nb_medium + F.n_hub > 0) + (F.n_warps > 0) +
+           (F.n_wide > 0) + 1;
 }
 
 }  // namespace fbp

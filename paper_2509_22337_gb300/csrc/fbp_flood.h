@@ -16,6 +16,7 @@ struct XP {
 constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread each
 constexpr int kFloodMediumMax = 256;   // rows up to this degree: one warp each
 constexpr int kFloodHubChunk = 1024;   // longer rows: chunks of this many entries (one block)
+constexpr int kFloodChunk = 8;         // iterations per captured CUDA graph
 
 struct FloodPlanDev {
     int32_t nb_small = 0;              // blocks of the one-thread-per-row role (degree 3..8)
@@ -28,6 +29,12 @@ struct FloodPlanDev {
     const int4 *hub = nullptr;         // [n_hub] {variable, row begin, row end, first chunk of the row}
     const int32_t *hub_nchunks = nullptr;  // [n_hub] chunks of the chunk's row
     XP *agg = nullptr;                 // [n_hub] partial product of each chunk
+    // phase 2: warps of whole consecutive factors; factors wider than a warp
+    // edge by edge
+    int32_t n_warps = 0;
+    const int4 *warps = nullptr;       // [n_warps] {first edge, end edge, first factor, end factor}
+    int32_t n_wide = 0;
+    const int32_t *wide = nullptr;     // [n_wide] edges of factors wider than a warp
     const int *done = nullptr;         // set once the run has converged
     // batched graphs: graph of each variable and factor; per-graph state
     const int32_t *vgraph = nullptr;
@@ -35,16 +42,23 @@ struct FloodPlanDev {
     BatchCtl batch;
 };
 
-// One flooding iteration (number `it`): phase 1 over every variable row,
-// phase 2 over every factor (in place on a2v), then the convergence check:
-// hist[it-1] receives the residual bits; done[0] is set at the first
-// iteration below tol and done[1] holds the last iteration executed.  Every
-// kernel returns at once when done[0] is set, so iterations can be queued in
-// batches without a host synchronisation per iteration.  `staged` = factor
-// row entries staged in shared memory per block (flood_smem_bytes of it).
-void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl,
-                     int staged, int it, float tol, unsigned *hist, int *done, cudaStream_t s);
-size_t flood_smem_bytes(int staged);
-void flood_prepare(size_t smem_bytes);
+// One flooding iteration: phase 1 over every variable row, phase 2 over
+// every factor (in place on a2v), then the convergence check.  done[4] is the
+// run's control block on the device: [0] 0 while running, 1 once converged
+// (or, for a batch, once no graph runs), 2 at the iteration limit; [1] the
+// last iteration executed (the device counts iterations itself, so queued or
+// captured iterations need no argument); [3] the iteration limit.
+// hist[it-1] receives iteration it's residual bits.  Every kernel returns at
+// once when done[0] is set, so iterations can be queued in batches, or
+// replayed from a captured graph, without a host synchronisation per
+// iteration.
+void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+                     unsigned *hist, int *done, cudaStream_t s);
+// A CUDA graph of `iters` consecutive flood_iterations (captured on a private
+// stream; launch it on any stream).
+cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+                          unsigned *hist, int *done, int iters, cudaGraphExec_t *exec);
+// Kernel launches of one flood_iteration.
+int flood_launches(const DevGraph &g, const FloodPlanDev &F);
 
 }  // namespace fbp

@@ -63,7 +63,11 @@ struct fbp_graph {
     // flooding plan
     FloodPlanDev flood;
     bool flood_ready = false;
-    int flood_staged = 0;
+    // captured chunk of flooding iterations and what it was captured for
+    cudaGraphExec_t flood_exec = nullptr;
+    int flood_exec_iters = 0;
+    float flood_exec_tol = 0.f;
+    const void *flood_exec_key[3] = {nullptr, nullptr, nullptr};  // messages, residual words, plan
     // per-iteration control
     unsigned *d_res = nullptr;
     unsigned long long *d_guards = nullptr;
@@ -112,5 +116,10 @@ int engine_check(fbp_graph *g);
 int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars, const uint8_t *ftype,
                      const float *fparam, const float *prior, const int8_t *evidence);
 int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_out, double *residual_out);
+// The graph's captured chunk of `iters` flooding iterations under plan F and
+// tolerance tol (captured again when any of them, the message buffer or the
+// residual words changed).
+int flood_exec_for(fbp_graph *g, const FloodPlanDev &F, float tol, int iters, cudaGraphExec_t *out);
+void flood_exec_drop(fbp_graph *g);
 
 }  // namespace fbp

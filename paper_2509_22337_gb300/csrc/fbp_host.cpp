@@ -218,13 +218,17 @@ int upload_erow(fbp_graph *g)
 int build_flood_plan(fbp_graph *g)
 {
     const HostCSR &h = g->h;
-    if (g->flood.small || g->flood.medium || g->flood.hub || g->flood.agg) {  // a rebuild after retuning
+    flood_exec_drop(g);
+    if (g->flood_ready) {  // a rebuild after retuning
         dfree(g, (void *)g->flood.small);
         dfree(g, (void *)g->flood.medium);
         dfree(g, (void *)g->flood.hub);
         dfree(g, (void *)g->flood.hub_nchunks);
         dfree(g, (void *)g->flood.agg);
+        dfree(g, (void *)g->flood.warps);
+        dfree(g, (void *)g->flood.wide);
         g->flood = FloodPlanDev{};
+        g->flood_ready = false;
     }
     FloodPlanDev F;
     std::vector<int32_t> small, medium;
@@ -268,13 +272,38 @@ int build_flood_plan(fbp_graph *g)
     F.hub = d_hub;
     F.hub_nchunks = d_hub_n;
     F.agg = d_agg;
-    int32_t mx = 0;
-    for (int32_t a0 = 0; a0 < h.na; a0 += 256) {
-        const int32_t a1 = std::min(a0 + 256, h.na);
-        mx = std::max(mx, (int32_t)(h.fptr[a1] - h.fptr[a0]));
+    // phase 2: consecutive whole factors packed into warps of at most 32 edges;
+    // a factor wider than a warp goes edge by edge to the wide list
+    std::vector<int4> warps;
+    std::vector<int32_t> wide;
+    {
+        int32_t a0 = 0;
+        auto close = [&](int32_t a1) {
+            if (a1 > a0) warps.push_back(make_int4((int)h.fptr[a0], (int)h.fptr[a1], a0, a1));
+        };
+        for (int32_t a = 0; a < h.na; ++a) {
+            const int64_t n = h.fptr[a + 1] - h.fptr[a];
+            if (n > 32) {
+                close(a);
+                for (int64_t e = h.fptr[a]; e < h.fptr[a + 1]; ++e) wide.push_back((int32_t)e);
+                a0 = a + 1;
+                continue;
+            }
+            if (h.fptr[a + 1] - h.fptr[a0] > 32) {
+                close(a);
+                a0 = a;
+            }
+        }
+        close(h.na);
     }
-    g->flood_staged = std::min(mx, 4096);  // 28 B of shared memory per staged entry
-    flood_prepare(flood_smem_bytes(g->flood_staged));
+    int4 *d_warps = nullptr;
+    int32_t *d_wide = nullptr;
+    if ((rc = upload(g, &d_warps, warps.data(), warps.size())) || (rc = upload(g, &d_wide, wide.data(), wide.size())))
+        return rc;
+    F.n_warps = (int32_t)warps.size();
+    F.warps = d_warps;
+    F.n_wide = (int32_t)wide.size();
+    F.wide = d_wide;
     g->flood = F;
     g->flood_ready = true;
     return FBP_OK;
@@ -339,6 +368,7 @@ extern "C" void fbp_graph_destroy(fbp_graph *g)
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
     else cudaDeviceSynchronize();
+    flood_exec_drop(g);
     std::vector<void *> all = g->owned;
     for (void *p : all) dfree(g, p);
     if (g->h_res) cudaFreeHost(g->h_res);
@@ -692,6 +722,7 @@ int run_per_level(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_ou
     int rc = ensure_res_cap(g, std::max(max_iters, 1));
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(max_iters, 1), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, g->stream));  // result and error words
     int grid = 1, cluster = 0;
     engine_shape(g, &grid, &cluster);
     int32_t it = 0;
@@ -747,9 +778,9 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     if (g->strategy != FBP_PARALL)
         return g->use_engine ? run_engine(g, max_iters, tol, iters_out, residual_out)
                              : run_per_level(g, max_iters, tol, iters_out, residual_out);
-    // flooding: iterations are queued in growing batches; a device-side check
-    // marks the run done and later kernels of the batch return at once
-    IterCtl ctl{g->d_res, g->d_guards};
+    // flooding: a captured chunk of kFloodChunk iterations is replayed in
+    // growing batches; the device counts iterations, marks the run done at
+    // convergence or at the limit, and later kernels return at once
     if (!g->v2a && dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
     if (!g->flood_ready) {
         int rc = build_flood_plan(g);
@@ -757,29 +788,55 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     }
     int rc = ensure_res_cap(g, std::max(max_iters, 1));
     if (rc) return rc;
+    if (max_iters == 0) return finish_run(g, 0, 0.0, FBP_NOT_CONVERGED, iters_out, residual_out);
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = flood_exec_for(g, g->flood, (float)tol, kFloodChunk, &exec))) return rc;
     CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
-    CUDA_TRY(cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, g->stream));
-    const int launches_per_iter = (h.nv > 0) + (g->flood.n_hub > 0) +
-                                  (g->flood.nb_small + g->flood.nb_medium + g->flood.n_hub > 0) + (h.na > 0) + 1;
-    int32_t next = 1, batch = 4;
-    bool done = false;
-    while (next <= max_iters && !done) {
-        const int32_t last = std::min(max_iters, next + batch - 1);
-        for (int32_t it = next; it <= last; ++it) {
-            flood_iteration(g->d, g->flood, g->a2v[g->cur], g->v2a, ctl, g->flood_staged, it, (float)tol,
-                            g->d_res_it, g->d_out, g->stream);
-            g->stats.kernel_launches += launches_per_iter;
+    g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
+    g->h_out[3] = max_iters;
+    CUDA_TRY(cudaMemcpyAsync(g->d_out, g->h_out, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, g->stream));
+    const int launches_per_iter = flood_launches(g->d, g->flood);
+    int32_t queued = 0, reps = 1;
+    while (queued < max_iters) {
+        for (int32_t r = 0; r < reps && queued < max_iters; ++r) {
+            CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+            queued += kFloodChunk;
+            g->stats.kernel_launches += (int64_t)kFloodChunk * launches_per_iter;
         }
-        CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream));
         CUDA_TRY(cudaStreamSynchronize(g->stream));
-        done = g->h_out[0] != 0;
-        next = last + 1;
-        batch = std::min(batch * 2, 64);
+        if (g->h_out[0] != 0) break;
+        reps = std::min(reps * 2, 8);
     }
-    const int32_t it = max_iters == 0 ? 0 : g->h_out[1];
+    const int32_t it = g->h_out[1];
     g->stats.updates += (int64_t)it * h.ne;
-    return finish_run(g, it, residual_at(g, it), done ? FBP_OK : FBP_NOT_CONVERGED, iters_out, residual_out);
+    return finish_run(g, it, residual_at(g, it), g->h_out[0] == 1 ? FBP_OK : FBP_NOT_CONVERGED, iters_out,
+                      residual_out);
+}
+
+int fbp::flood_exec_for(fbp_graph *g, const FloodPlanDev &F, float tol, int iters, cudaGraphExec_t *out)
+{
+    const void *key[3] = {g->a2v[g->cur], g->d_res_it, F.warps};
+    if (g->flood_exec && g->flood_exec_iters == iters && g->flood_exec_tol == tol &&
+        std::equal(key, key + 3, g->flood_exec_key)) {
+        *out = g->flood_exec;
+        return FBP_OK;
+    }
+    flood_exec_drop(g);
+    IterCtl ctl{g->d_res, g->d_guards};
+    CUDA_TRY(flood_capture(g->d, F, g->a2v[g->cur], g->v2a, ctl, tol, g->d_res_it, g->d_out, iters, &g->flood_exec));
+    g->flood_exec_iters = iters;
+    g->flood_exec_tol = tol;
+    std::copy(key, key + 3, g->flood_exec_key);
+    *out = g->flood_exec;
+    return FBP_OK;
+}
+
+void fbp::flood_exec_drop(fbp_graph *g)
+{
+    if (g->flood_exec) cudaGraphExecDestroy(g->flood_exec);
+    g->flood_exec = nullptr;
+    g->flood_exec_iters = 0;
 }
 
 // RESIDUAL strategy: the classes of the next iteration come from the previous
@@ -821,6 +878,7 @@ int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters
                                  cudaMemcpyDeviceToDevice, g->stream));
         CUDA_TRY(cudaMemsetAsync(g->dres, 0, sizeof(float) * h.ne, g->stream));
         CUDA_TRY(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, g->stream));
+        CUDA_TRY(cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, g->stream));  // result and error words
         EngineArgs A = engine_args(g);
         A.n_halves = 1;
         A.res = g->d_res_it + (it - 1);

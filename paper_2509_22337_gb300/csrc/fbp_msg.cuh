@@ -97,40 +97,44 @@ __device__ __forceinline__ P2 norm_max(P2 m)
     return P2{m.m0 == mx ? 1.f : m.m0 * inv, m.m1 == mx ? 1.f : m.m1 * inv};
 }
 
-// Factor-to-variable message of factor (type, p) with n variables to its
-// variable at position i; getm(j) yields the incoming v->a message of position
-// j scaled so that its larger entry is 1.  The closed forms above are written
-// without a branch on the factor type: every type's message is a combination
-// of the five products (taken over the premises other than the target), with
-// coefficients selected per type:
+// Products over a factor's premises other than the target (see the closed
+// forms above), accumulated in premise order.  A message enters scaled so
+// that its larger entry is 1; the sums s_j lie in [1, 2], so only Ps can grow,
+// and all five are scaled down together by 2^-60 past 2^60 (the message is
+// homogeneous in them).
+struct Acc5 {
+    float P1 = 1.f, P0 = 1.f, Ps = 1.f, D = 0.f, D0 = 0.f;
+};
+
+__device__ __forceinline__ void acc5_add(Acc5 &a, P2 m)
+{
+    const float s = m.m0 + m.m1;
+    a.D = fmaf(a.D, s, a.P1 * m.m0);
+    a.D0 = fmaf(a.D0, s, a.P0 * m.m1);
+    a.P1 *= m.m1;
+    a.P0 *= m.m0;
+    a.Ps *= s;
+    if (a.Ps > 0x1p60f) {
+        a.P1 *= 0x1p-60f; a.P0 *= 0x1p-60f; a.Ps *= 0x1p-60f; a.D *= 0x1p-60f; a.D0 *= 0x1p-60f;
+    }
+}
+
+// The message of factor (type, p) to its output (to_output) or to a premise,
+// from the products over the other premises and the output's incoming message
+// my (unused for the output).  Every type's message is a combination of the
+// five products with coefficients selected per type, so a warp that holds
+// factors of different types runs one instruction stream:
 //   target = output:   mu0 = a0 P1 + a1 D + a2 P0,   mu1 = b0 P1 + b1 D + b2 D0 + b3 P0
 //   target = premise:  mu0 = c0 Ps + c1 P0 + c2 D0,  mu1 = d0 P1 + d1 D + d2 Ps
 // (NOT reads its single premise through P1/P0; EQ treats the last variable
 // like the output; PRIOR has no premises, so P1 = P0 = 1 and D = D0 = 0.)
-// A warp that holds factors of different types runs one instruction stream.
-template <class GetM>
-__device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM getm)
+__device__ __forceinline__ P2 a2v_finish(int type, float p, bool to_output, const Acc5 &A, P2 my)
 {
-    const int y = n - 1;
-    float P1 = 1.f, P0 = 1.f, Ps = 1.f, D = 0.f, D0 = 0.f;
-    for (int j = 0; j < y; ++j) {
-        if (j == i) continue;
-        const P2 m = getm(j);
-        const float s = m.m0 + m.m1;
-        D = fmaf(D, s, P1 * m.m0);
-        D0 = fmaf(D0, s, P0 * m.m1);
-        P1 *= m.m1;
-        P0 *= m.m0;
-        Ps *= s;
-        if (Ps > 0x1p60f) {
-            P1 *= 0x1p-60f; P0 *= 0x1p-60f; Ps *= 0x1p-60f; D *= 0x1p-60f; D0 *= 0x1p-60f;
-        }
-    }
     const unsigned t = 1u << type;
     constexpr unsigned AND = 1u << kTypeAND, OR = 1u << kTypeOR, NOT = 1u << kTypeNOT, EQ = 1u << kTypeEQ,
                        NI = 1u << kTypeNOISY_IMPLY, NA = 1u << kTypeNOISY_AND, PR = 1u << kTypePRIOR;
     const float q = 1.f - p;
-    if (i == y) {
+    if (to_output) {
         const float a0 = (t & NOT) ? 1.f : (t & (NA | NI | PR)) ? q : 0.f;
         const float a1 = (t & (AND | NA | NI)) ? 1.f : 0.f;
         const float a2 = (t & (OR | EQ)) ? 1.f : 0.f;
@@ -138,9 +142,8 @@ __device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM 
         const float b1 = (t & NI) ? 1.f : 0.f;
         const float b2 = (t & OR) ? 1.f : 0.f;
         const float b3 = (t & NOT) ? 1.f : 0.f;
-        return P2{fmaf(a0, P1, fmaf(a1, D, a2 * P0)), fmaf(b0, P1, fmaf(b1, D, fmaf(b2, D0, b3 * P0)))};
+        return P2{fmaf(a0, A.P1, fmaf(a1, A.D, a2 * A.P0)), fmaf(b0, A.P1, fmaf(b1, A.D, fmaf(b2, A.D0, b3 * A.P0)))};
     }
-    const P2 my = getm(y);
     const float sy = my.m0 + my.m1, w = fmaf(p, my.m1, q * my.m0);
     const float c0 = (t & (AND | NA)) ? my.m0 : (t & NOT) ? my.m1 : (t & NI) ? sy : 0.f;
     const float c1 = (t & (OR | EQ)) ? my.m0 : 0.f;
@@ -148,7 +151,23 @@ __device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM 
     const float d0 = (t & (AND | EQ)) ? my.m1 : (t & (NA | NI)) ? w : 0.f;
     const float d1 = (t & (AND | NA)) ? my.m0 : (t & NI) ? sy : 0.f;
     const float d2 = (t & OR) ? my.m1 : (t & NOT) ? my.m0 : 0.f;
-    return P2{fmaf(c0, Ps, fmaf(c1, P0, c2 * D0)), fmaf(d0, P1, fmaf(d1, D, d2 * Ps))};
+    return P2{fmaf(c0, A.Ps, fmaf(c1, A.P0, c2 * A.D0)), fmaf(d0, A.P1, fmaf(d1, A.D, d2 * A.Ps))};
+}
+
+// Factor-to-variable message of factor (type, p) with n variables to its
+// variable at position i; getm(j) yields the incoming v->a message of position
+// j scaled so that its larger entry is 1.
+template <class GetM>
+__device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM getm)
+{
+    const int y = n - 1;
+    Acc5 A;
+    for (int j = 0; j < y; ++j) {
+        if (j == i) continue;
+        acc5_add(A, getm(j));
+    }
+    if (i == y) return a2v_finish(type, p, true, A, P2{1.f, 1.f});
+    return a2v_finish(type, p, false, A, getm(y));
 }
 
 // Hardware reciprocal approximation (rcp.approx.f32: relative error within a

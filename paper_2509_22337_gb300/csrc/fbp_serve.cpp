@@ -245,17 +245,17 @@ int fbp_server::launch_chunk(Sess &s)
 {
     fbp_graph *g = s.g;
     if (s.strategy == FBP_PARALL) {
-        IterCtl ctl{g->d_res, g->d_guards};
+        // one replay of the session's captured chunk of iterations
         const int32_t k = cfg.iters_per_tick > 0 ? cfg.iters_per_tick : 16;
-        const int32_t last = std::min(s.max_iters, s.it_done + k);
-        const int per_iter = (g->h.nv > 0) + (g->flood.n_hub > 0) +
-                             (g->flood.nb_small + g->flood.nb_medium + g->flood.n_hub > 0) + (g->h.na > 0) + 1;
-        for (int32_t it = s.it_done + 1; it <= last; ++it) {
-            flood_iteration(g->d, g->flood, g->a2v[g->cur], g->v2a, ctl, g->flood_staged, it, (float)s.tol,
-                            g->d_res_it, g->d_out, s.stream);
-            stats.kernel_launches += per_iter;
+        if (s.max_iters > 0) {
+            cudaGraphExec_t exec = nullptr;
+            int rc = flood_exec_for(g, g->flood, (float)s.tol, k, &exec);
+            if (rc) return rc;
+            cudaError_t e = cudaGraphLaunch(exec, s.stream);
+            if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "chunk: %s", cudaGetErrorString(e));
+            stats.kernel_launches += (int64_t)k * flood_launches(g->d, g->flood);
         }
-        s.it_done = last;
+        s.it_done = std::min(s.max_iters, s.it_done + k);
     } else if (s.max_iters > 0) {
         EngineArgs A = engine_args(g);
         A.res = g->d_res_it;
@@ -290,7 +290,9 @@ int fbp_server::start(Sess &s, int64_t ticket)
         r.t_start = Clock::now();
     }
     cudaError_t e = cudaEventRecord(s.ev_start, s.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_out, 0, sizeof(int32_t) * 4, s.stream);
+    g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
+    g->h_out[3] = s.max_iters;  // the flooding kernels' iteration limit
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_out, g->h_out, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), s.stream);
     if (s.strategy == FBP_PARALL) {
         if (e == cudaSuccess) e = cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, s.stream);
@@ -317,7 +319,7 @@ int fbp_server::finish_iterating(Sess &s)
     int status = FBP_NOT_CONVERGED;
     if (s.strategy == FBP_PARALL) {
         it = s.max_iters == 0 ? 0 : g->h_out[1];
-        status = g->h_out[0] ? FBP_OK : FBP_NOT_CONVERGED;
+        status = g->h_out[0] == 1 ? FBP_OK : FBP_NOT_CONVERGED;
     } else if (s.max_iters > 0) {
         if (engine_owner == s.id) engine_owner = -1;
         if (g->h_out[2]) return fail(FBP_ERR_TIMEOUT, "a device-side barrier wait expired");

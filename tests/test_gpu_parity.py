@@ -315,3 +315,28 @@ def test_engine_cluster_mode_does_not_change_results(fbp, cluster):
         b = H.messages()
         H.close()
         assert np.array_equal(a, b), (g.name, cluster)
+
+
+def test_residual_reaches_the_oracles_fixed_points(fbp):
+    """RESIDUAL's levels come from float residuals, so only its outcome is
+    compared: the GPU run converges where the FP64 oracle's RESIDUAL run
+    does, and its marginals match both the oracle's RESIDUAL and flooding
+    fixed points within 1e-5."""
+    graphs = [gen.random_tree(14, seed=500 + s) for s in range(4)]
+    graphs += [gen.smartfl(n_layers=12, width=40, seed=31, planted=True),
+               gen.random_loopy(60, 50, seed=510)]
+    checked = 0
+    for g in graphs:
+        b_res = oracle_run(g, "RESIDUAL", 400, 1e-7)
+        b_par = oracle_run(g, "PARALL", 400, 1e-7)
+        if not (b_res["converged"] and b_par["converged"]):
+            continue
+        if not (in_fp32_range(b_res) and in_fp32_range(b_par)):
+            continue
+        a = gpu_run(fbp, g, "RESIDUAL", 400, 1e-7)
+        assert a["status"] == fbp.FBP_OK, (g.name, a["iters"], a["residual"])
+        assert np.abs(a["p"] - b_res["p"]).max() <= TOL_P, g.name
+        assert np.abs(a["p"] - b_par["p"]).max() <= TOL_P, g.name
+        assert a["stats"]["updates"] <= a["iters"] * g.n_edges  # skipped factors are not updated
+        checked += 1
+    assert checked >= 4

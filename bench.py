@@ -456,16 +456,20 @@ def run_gpu(args):
     sweeps = st["iters"]
     launches_per_step = max(st["kernel_launches"], 1)
     kernel_ms = float(np.median(run_ms))
-    per_launch_ms = kernel_ms / launches_per_step
     if strategy == "PARALL":
-        kname = "k_v2a_flood + k_a2v_flood"
+        # the unit is one flooding iteration (its five kernels, replayed from
+        # a captured CUDA graph): algorithmic bytes per iteration over the
+        # device time per iteration
+        kname = "flooding iteration (k_v2a_lean, k_hub_partials, k_v2a_rest, k_a2v_lanes, k_flood_check)"
         kkey = "flood"
-        bytes_per_launch = algorithmic_bytes_flood(g) * sweeps / launches_per_step
+        launches_per_step = max(sweeps, 1)
+        bytes_per_launch = algorithmic_bytes_flood(g)
     else:
         kname = "k_engine (persistent level engine, one launch per run)"
         kkey = "k_engine"
         halves = 2 if strategy == "TOPO_FB" else 1
         bytes_per_launch = algorithmic_bytes_per_half(g) * halves * sweeps / launches_per_step
+    per_launch_ms = kernel_ms / launches_per_step
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0}
     peak = float(peaks.get("hbm_gbs", 6800.0))

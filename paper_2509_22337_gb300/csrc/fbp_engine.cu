@@ -42,7 +42,9 @@ namespace {
 constexpr int kBlock = 256;    // threads per block (grid mode)
 constexpr int kClusterBlock = 512;  // threads per block in cluster mode: 16 x 16 warps hold a level
 constexpr int kMaxFan = 32;    // largest factor held by one warp (larger: per-edge path)
-constexpr int kPre = 16;       // row entries of a lane prefetched into registers
+constexpr int kPreDeep = 16;   // row entries of a lane prefetched: levels that fit the grid in one pass
+constexpr int kPreWide = 8;    // levels of several passes per level (throughput, not latency, bound)
+constexpr int kPreAt = 8;      // row entries per step of the per-edge path (factors wider than a warp)
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
@@ -96,10 +98,10 @@ __device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P,
 {
     const int4 er = __ldg(A.erow + q);
     P2 m = dec(__ldg(A.g.phi + er.z));
-    for (int k0 = er.x; k0 < er.y; k0 += kPre) {
-        float rr[kPre];
+    for (int k0 = er.x; k0 < er.y; k0 += kPreAt) {
+        float rr[kPreAt];
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
+        for (int u = 0; u < kPreAt; ++u) {
             rr[u] = 1.f;
             if (k0 + u < er.y) {
                 const int2 ev = __ldg(P.vel + k0 + u);
@@ -107,7 +109,7 @@ __device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P,
             }
         }
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
+        for (int u = 0; u < kPreAt; ++u) {
             m = mul(m, dec(rr[u]));
             if (u & 1) resc(m);
         }
@@ -116,6 +118,7 @@ __device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P,
 }
 
 // A lane's read-only state for one level.
+template <int kPre>
 struct Pre {
     int4 rec;          // lane record: {edge q or -1, first | n<<5 | type<<11 | target<<14, p bits, variable}
     float phi;
@@ -143,7 +146,8 @@ __device__ __forceinline__ void prefetch_a(PreA &a, const LevelPlanDev &P, int s
 
 // The second round (unary potential and the first row entries), from a
 // completed first round.
-__device__ __forceinline__ void prefetch_b(Pre &s, const PreA &a, const EngineArgs &A, const LevelPlanDev &P,
+template <int kPre>
+__device__ __forceinline__ void prefetch_b(Pre<kPre> &s, const PreA &a, const EngineArgs &A, const LevelPlanDev &P,
                                            int La)
 {
     s.rec = a.rec;
@@ -170,7 +174,8 @@ __device__ __forceinline__ void prefetch_b(Pre &s, const PreA &a, const EngineAr
     s.kend = er.y;
 }
 
-__device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
+template <int kPre>
+__device__ __forceinline__ void prefetch(Pre<kPre> &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
                                          int s1)
 {
     PreA a;
@@ -181,7 +186,8 @@ __device__ __forceinline__ void prefetch(Pre &s, const EngineArgs &A, const Leve
 // One lane's share of a level: its position's v->a product, then (if its edge
 // is in the level) its factor's closed form a->v message.  Called by whole
 // warps (the __syncwarp()s).
-__device__ __forceinline__ void run_lane(const Pre &s, const EngineArgs &A, const LevelPlanDev &P, int La,
+template <int kPre>
+__device__ __forceinline__ void run_lane(const Pre<kPre> &s, const EngineArgs &A, const LevelPlanDev &P, int La,
                                          const float *cur, float *nxt, P2 *sm, float &rmax,
                                          unsigned long long &ng)
 {
@@ -249,7 +255,7 @@ __device__ __forceinline__ void run_lane(const Pre &s, const EngineArgs &A, cons
         // per-graph residual: one atomic per graph present in the warp
         const unsigned grp = __match_any_sync(0xffffffffu, q >= 0 ? graph : -1);
         const unsigned bits = __reduce_max_sync(grp, __float_as_uint(d));
-        if (q >= 0 && lane == __ffs(grp) - 1 && bits) atomicMax(A.batch.res + graph, bits);
+        if (q >= 0 && lane == __ffs(grp) - 1 && bits) max_bits(A.batch.res + graph, bits);
     }
     __syncwarp();
 }
@@ -284,7 +290,7 @@ __device__ __forceinline__ LevelPlanDev plan_at(const EngineArgs &A, int h)
     return h == 0 ? A.half[0] : A.half[1];
 }
 
-template <bool kCluster, int kThreads>
+template <bool kCluster, int kThreads, int kPre>
 __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
 {
     __shared__ P2 s_m[kThreads];
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
     int it, status = 1, failed = 0;
     const bool empty = A.n_halves == 0 ||
                        (A.half[0].n_levels == 0 && (A.n_halves < 2 || A.half[1].n_levels == 0));
-    Pre pre;
+    Pre<kPre> pre;
     if (!empty) {
         int h0 = 0;
         while (plan_at(A, h0).n_levels == 0) ++h0;
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                 prefetch_a(next, Pn, __ldg(Pn.lane_ptr + Ln) + my0, __ldg(Pn.lane_ptr + Ln + 1));
                 run_lane(pre, A, P, La, cur, nxt, sm, rmax, ng);
                 for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
-                    Pre more;
+                    Pre<kPre> more;
                     prefetch(more, A, P, La, slot, s1);
                     run_lane(more, A, P, La, cur, nxt, sm, rmax, ng);
                 }
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                 }
                 if (L + 1 == P.n_levels && h + 1 == A.n_halves) {
                     const float bm = block_max(rmax);
-                    if (threadIdx.x == 0 && bm > 0.f) atomicMax(A.res + (it - 1), __float_as_uint(bm));
+                    if (threadIdx.x == 0 && bm > 0.f) max_bits(A.res + (it - 1), __float_as_uint(bm));
                 }
                 if (kCluster) {
                     cluster_arrive();
@@ -418,15 +424,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
 int engine_block() { return kBlock; }
 int engine_max_fan() { return kMaxFan; }
 
+// Blocks of a cooperative grid that can be co-resident: for the shallow
+// (wide-level) variant, and for the deep-prefetch variant (more registers).
+static int cap_of(const void *kernel)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    return per_sm * num_sms() > 0 ? per_sm * num_sms() : 1;
+}
+
 int engine_max_grid()
 {
     static int cap = 0;
-    if (!cap) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine<false, kBlock>, kBlock, 0);
-        cap = per_sm * num_sms();
-        if (cap < 1) cap = 1;
-    }
+    if (!cap) cap = cap_of((const void *)k_engine<false, kBlock, kPreWide>);
+    return cap;
+}
+
+static int engine_deep_grid()
+{
+    static int cap = 0;
+    if (!cap) cap = cap_of((const void *)k_engine<false, kBlock, kPreDeep>);
     return cap;
 }
 
@@ -437,7 +454,7 @@ int engine_cluster_size()
     static int size = -1;
     if (size < 0) {
         size = 0;
-        cudaFuncSetAttribute(k_engine<true, kClusterBlock>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_engine<true, kClusterBlock, kPreDeep>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(c);
@@ -450,7 +467,7 @@ int engine_cluster_size()
             cfg.attrs = &attr;
             cfg.numAttrs = 1;
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k_engine<true, kClusterBlock>, &cfg) == cudaSuccess && n > 0) {
+            if (cudaOccupancyMaxActiveClusters(&n, k_engine<true, kClusterBlock, kPreDeep>, &cfg) == cudaSuccess && n > 0) {
                 size = c;
                 break;
             }
@@ -475,13 +492,20 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
         attr.val.clusterDim.z = 1;
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_engine<true, kClusterBlock>, args);
+        return cudaLaunchKernelEx(&cfg, k_engine<true, kClusterBlock, kPreDeep>, args);
     }
     const int cap = engine_max_grid();
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     void *params[] = {&args};
-    return cudaLaunchCooperativeKernel((void *)k_engine<false, kBlock>, dim3(grid), dim3(kBlock), params, 0, s);
+    // levels that the grid holds in one pass are latency bound: prefetch
+    // deep (when the grid fits that variant's co-residency); wider levels run
+    // several passes and are throughput bound: the lighter variant, whose
+    // grid may hold two blocks per SM.  Both compute the same messages.
+    const bool deep = grid <= engine_deep_grid() && (long long)a.max_lanes <= (long long)grid * kBlock;
+    return cudaLaunchCooperativeKernel(deep ? (void *)k_engine<false, kBlock, kPreDeep>
+                                            : (void *)k_engine<false, kBlock, kPreWide>,
+                                       dim3(grid), dim3(kBlock), params, 0, s);
 }
 
 }  // namespace fbp

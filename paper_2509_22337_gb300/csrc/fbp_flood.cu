@@ -301,7 +301,7 @@ __device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph,
 {
     const unsigned grp = __match_any_sync(0xffffffffu, graph);
     const unsigned bits = __reduce_max_sync(grp, __float_as_uint(d));
-    if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) atomicMax(F.batch.res + graph, bits);
+    if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) max_bits(F.batch.res + graph, bits);
 }
 
 // One lane per message: each warp holds whole factors (consecutive in the
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
         return;
     }
     const float bm = block_max(d);
-    if (threadIdx.x == 0 && bm > 0.f) atomicMax(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
+    if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
 // Factors wider than a warp: one thread per edge, the closed form over the
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodP
         return;
     }
     const float bm = block_max(d);
-    if (threadIdx.x == 0 && bm > 0.f) atomicMax(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
+    if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
 // End of an iteration of a batch: per-graph bookkeeping as in the persistent

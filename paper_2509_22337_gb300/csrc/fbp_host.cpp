@@ -649,6 +649,7 @@ EngineArgs engine_args(fbp_graph *g)
     A.bar = g->d_bar;
     A.out = g->d_out;
     A.spin_limit = g->spin_limit;
+    for (auto &ls : g->halves) A.max_lanes = std::max(A.max_lanes, ls.max_lanes);
     return A;
 }
 

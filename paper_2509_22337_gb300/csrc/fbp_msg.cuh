@@ -201,6 +201,15 @@ __device__ __forceinline__ float delta_p1_fast(float rn, float ro)
     return (1.f - an) * rcp_approx(2.f * (1.f + an)) + (1.f - ao) * rcp_approx(2.f * (1.f + ao));
 }
 
+// Raise a max word to `bits` (the bits of a non-negative float, so that the
+// integer and float orders agree).  The word only grows while it collects a
+// maximum, so a read that already shows at least `bits` makes the atomic
+// unnecessary; this keeps thousands of blocks from serialising on one word.
+__device__ __forceinline__ void max_bits(unsigned *word, unsigned bits)
+{
+    if (bits > __ldcg(word)) atomicMax(word, bits);
+}
+
 // Warp max of a non-negative float, then block max via shared memory; the
 // result is valid in thread 0.  Every thread of the block must call it.
 __device__ __forceinline__ float block_max(float v)

@@ -340,3 +340,17 @@ def test_residual_reaches_the_oracles_fixed_points(fbp):
         assert a["stats"]["updates"] <= a["iters"] * g.n_edges  # skipped factors are not updated
         checked += 1
     assert checked >= 4
+
+
+def test_engine_prefetch_variants_agree(fbp):
+    """A grid that holds a level in one pass runs the deep-prefetch engine, a
+    small grid (several passes per level) the shallow one: same messages."""
+    g = gen.smartfl(n_layers=5, width=4000, seed=64)
+    out = []
+    for grid in (152, 6):
+        G = fbp.Graph(g, "TOPO_FB")
+        G.set_option(fbp.FBP_OPT_ENGINE_GRID, grid)
+        G.run(4, 0.0)
+        out.append(G.messages())
+        G.close()
+    assert np.array_equal(out[0], out[1])

@@ -117,6 +117,33 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms: float, units: float, device: str = "cuda"):
+    """The job's time and work over all ranks: the slowest rank's time and the
+    sum of the units every rank processed (unchanged for one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def shard(sizes, world: int, rank: int) -> list:
+    """Independent units (graphs, sessions) of the given sizes, bin-packed over
+    the ranks: largest first onto the least-loaded rank.  Returns this rank's
+    unit indices in ascending order; every unit goes to exactly one rank."""
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += sizes[i]
+    return [i for i in range(len(sizes)) if owner[i] == rank]
+
+
 def algorithmic_bytes_per_half(g):
     """Bytes one half-iteration (one pass over every level of one level list)
     of the persistent level engine must move at minimum: per edge the old and
@@ -227,15 +254,7 @@ def run_batched(args, rank, world, local):
     B2.close()
     h2d = sum(g.nbytes() for g in graphs)
     d2h = sum(4 * g.n_vars for g in graphs)
-    t_max, tot = total, upd
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([float(upd)], device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot = u.item()
+    t_max, tot = aggregate(total, upd)
     n = len(graphs)
     if rank == 0:
         line = {
@@ -278,24 +297,32 @@ def run_serving(args, rank, world, local):
         raise SystemExit(f"the stream holds {len(stream)} requests, {need} asked for")
     srv = SV.Server(hbm_budget_bytes=120 << 30, max_inflight=args.serve_inflight,
                     iters_per_tick=args.serve_tick)
+    # sessions are independent: with several GPUs each rank serves a bin-packed
+    # share of them and the requests addressed to those (no collective)
+    mine = shard([g.n_edges for g in sessions], world, rank)
     t0 = time.perf_counter()
-    sids = [srv.open(g, strategy, max_iters, tol) for g in sessions]
+    sids = {i: srv.open(sessions[i], strategy, max_iters, tol) for i in mine}
+    glob = {v: k for k, v in sids.items()}  # server session id -> workload session index
     while srv.stats()["sessions_warming"] > 0:
         time.sleep(0.01)
     load_s = time.perf_counter() - t0
 
     def replay(window):
-        """Submit each request at its arrival time (relative to the window's
-        first), wait for all; returns (infos, wall seconds)."""
+        """Submit each of this rank's requests at its arrival time (relative to
+        the window's first), wait for all; returns (infos, wall seconds)."""
         base = float(window["t"][0])
         tickets = []
         start = time.perf_counter()
         for r in window:
+            if int(r["session"]) not in sids:
+                continue
             delay = (float(r["t"]) - base) - (time.perf_counter() - start)
             if delay > 0:
                 time.sleep(delay)
             tickets.append(srv.submit(sids[int(r["session"])], int(r["var"]), int(r["value"])))
         infos = [srv.wait(t)[0] for t in tickets]
+        for i in infos:
+            i["session"] = glob[i["session"]]
         return infos, time.perf_counter() - start
 
     for w in range(args.warmup):  # warm-up windows: the end of the stream
@@ -308,6 +335,12 @@ def run_serving(args, rank, world, local):
             infos += i
             wall += dt
     st1 = srv.stats()
+    if world > 1:  # every rank's requests into the percentiles; the slowest rank's time
+        import torch.distributed as dist
+        parts = [None] * world
+        dist.all_gather_object(parts, infos)
+        infos = [i for p in parts for i in p]
+        wall, _ = aggregate(wall, 0.0)
     lat = np.array([i["latency_ms"] for i in infos])
     svc = np.array([i["latency_ms"] - i["queue_ms"] for i in infos])
     dev = np.array([i["device_ms"] for i in infos])
@@ -325,6 +358,8 @@ def run_serving(args, rank, world, local):
     # cold-start per-request plain path on a sample of the same requests: a new
     # graph with the session's evidence so far, a run from uniform messages,
     # marginals to the host
+    if rank != 0:
+        return
     cold = []
     evid = [np.array(g.evidence, copy=True) for g in sessions]
     for r in stream[: per * args.steps]:
@@ -352,7 +387,8 @@ def run_serving(args, rank, world, local):
                    "n_vars": int(sum(g.n_vars for g in sessions)), "n_edges": int(sum(g.n_edges for g in sessions)),
                    "requests_per_step": per, "offered_rate_req_s": 2000.0, "max_inflight": args.serve_inflight,
                    "iters_per_tick": args.serve_tick, "hbm_budget_gb": 120,
-                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+                   "l2": "inputs larger than L2",
+                   "parallelism": f"sessions bin-packed over {world} GPU(s)" if world > 1 else "replicas1"},
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
                        "note": "submission to result on the host, queueing under the offered rate included"},
         "service_ms": {"p50": round(float(np.percentile(svc, 50)), 3), "p99": round(float(np.percentile(svc, 99)), 3)},
@@ -440,16 +476,7 @@ def run_gpu(args):
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(ms))
     st = G.stats()
-    t_max = total_ms
-    tot_updates = updates
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([float(updates)], device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot_updates = u.item()
+    t_max, tot_updates = aggregate(total_ms, updates)
     value = tot_updates / (t_max / 1e3)
 
     # roofline of the dominant kernel

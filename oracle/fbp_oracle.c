@@ -31,8 +31,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* factor type codes (input format) */
-enum { O_AND = 0, O_OR = 1, O_NOT = 2, O_EQ = 3, O_NOISY_IMPLY = 4, O_NOISY_AND = 5, O_PRIOR = 6 };
+/* factor type codes (input format); O_TERMS: a generic factor whose local
+ * structure is given explicitly as an indicator array (Sec. 4.3.2) */
+enum { O_AND = 0, O_OR = 1, O_NOT = 2, O_EQ = 3, O_NOISY_IMPLY = 4, O_NOISY_AND = 5, O_PRIOR = 6,
+       O_TERMS = 7 };
 /* strategy codes (input format) */
 enum { S_PARALL = 0, S_SEQFIX = 1, S_TOPO = 2, S_TOPO_FB = 3, S_RESIDUAL = 4, S_CUSTOM = 5 };
 
@@ -248,10 +250,77 @@ og_graph *orc_graph_new(int32_t nv, int32_t na, const int64_t *fptr, const int32
         int b = (int)(fptr[a + 1] - fptr[a]);
         g->ind[a] = (int8_t *)malloc((size_t)(b > 0 ? b : 1) * lmax);
         g->tw[a] = (double *)malloc(sizeof(double) * lmax);
+        if (ftype[a] == O_TERMS) {  /* terms come from orc_set_terms */
+            if (b < 1) { orc_graph_free(g); return NULL; }
+            g->nterms[a] = 0;
+            continue;
+        }
         g->nterms[a] = orc_terms(ftype[a], b, g->fparam[a], g->ind[a], g->tw[a], lmax);
         if (g->nterms[a] < 0) { orc_graph_free(g); return NULL; }
     }
     return g;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Explicit local structure of the generic (O_TERMS) factors: the indicator   */
+/* array of Sec. 4.3.2 and its weights, evaluated by Algorithm 1 like every   */
+/* other factor.  Factor a's terms are term_ptr[a] .. term_ptr[a+1]-1; its    */
+/* indicators are a block of (terms x variables) values, term after term, in  */
+/* the factor's variable order, blocks in factor order; a value is 0, 1 or    */
+/* -1 (the variable is free in that term).  Other factors must have no terms. */
+/* The term store is re-laid with a larger common stride when needed.         */
+/* ------------------------------------------------------------------------ */
+int orc_set_terms(og_graph *g, const int64_t *term_ptr, const int8_t *term_ind, const double *term_w)
+{
+    int need = g->lmax;
+    if (term_ptr[0] != 0) return -1;
+    for (int a = 0; a < g->na; a++) {
+        int64_t l = term_ptr[a + 1] - term_ptr[a];
+        if (l < 0 || (g->ftype[a] != O_TERMS && l != 0)) return -1;
+        if (l > need) need = (int)l;
+    }
+    int64_t off = 0;
+    for (int a = 0; a < g->na; a++) {
+        int b = (int)(g->fptr[a + 1] - g->fptr[a]);
+        for (int64_t t = term_ptr[a]; t < term_ptr[a + 1]; t++) {
+            if (!(term_w[t] >= 0.0) || !isfinite(term_w[t])) return -1;
+            for (int j = 0; j < b; j++) {
+                int8_t c = term_ind[off + (t - term_ptr[a]) * b + j];
+                if (c < -1 || c > 1) return -1;
+            }
+        }
+        off += (term_ptr[a + 1] - term_ptr[a]) * b;
+    }
+    if (need > g->lmax) {  /* re-lay every factor's terms with the new stride */
+        for (int a = 0; a < g->na; a++) {
+            int b = (int)(g->fptr[a + 1] - g->fptr[a]);
+            int8_t *ind = (int8_t *)malloc((size_t)(b > 0 ? b : 1) * need);
+            double *tw = (double *)malloc(sizeof(double) * need);
+            for (int j = 0; j < b; j++)
+                for (int t = 0; t < g->nterms[a]; t++) ind[j * need + t] = g->ind[a][j * g->lmax + t];
+            for (int t = 0; t < g->nterms[a]; t++) tw[t] = g->tw[a][t];
+            free(g->ind[a]); free(g->tw[a]);
+            g->ind[a] = ind; g->tw[a] = tw;
+        }
+        g->lmax = need;
+    }
+    off = 0;
+    for (int a = 0; a < g->na; a++) {
+        int b = (int)(g->fptr[a + 1] - g->fptr[a]);
+        int l = (int)(term_ptr[a + 1] - term_ptr[a]);
+        if (g->ftype[a] == O_TERMS) {
+            for (int t = 0; t < l; t++) {
+                for (int j = 0; j < b; j++) {
+                    int8_t c = term_ind[off + (int64_t)t * b + j];
+                    g->ind[a][j * g->lmax + t] = (int8_t)(c < 0 ? WILD : c);
+                }
+                g->tw[a][t] = term_w[term_ptr[a] + t];
+            }
+            g->nterms[a] = l;
+        }
+        off += (int64_t)l * b;
+    }
+    return 0;
 }
 
 int64_t orc_num_edges(const og_graph *g) { return g->ne; }

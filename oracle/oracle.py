@@ -66,6 +66,8 @@ def lib():
             L.orc_graph_free.restype = None
             L.orc_set_evidence.argtypes = [C.c_void_p, C.c_int32, C.c_int8, C.c_float]
             L.orc_set_evidence.restype = C.c_int
+            L.orc_set_terms.argtypes = [C.c_void_p, _i64, _i8, _f64]
+            L.orc_set_terms.restype = C.c_int
             L.orc_ranks.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, _i64]
             L.orc_ranks.restype = C.c_int
             for fn in (L.orc_levels_literal, L.orc_levels_nbr):
@@ -127,6 +129,11 @@ class Oracle:
             np.ascontiguousarray(g.prior_p1, np.float32), np.ascontiguousarray(g.evidence, np.int8))
         if not self._h:
             raise ValueError("oracle rejected the graph")
+        if getattr(g, "terms", None) is not None:
+            tp, ti, tw = g.terms
+            if lib().orc_set_terms(self._h, np.ascontiguousarray(tp, np.int64), np.ascontiguousarray(ti, np.int8),
+                                   np.ascontiguousarray(tw, np.float64)) != 0:
+                raise ValueError("oracle rejected the term lists")
 
     def __del__(self):
         h = getattr(self, "_h", None)

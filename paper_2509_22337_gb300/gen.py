@@ -15,6 +15,7 @@ Factor type codes (the input format; each side of the library/oracle boundary
 declares its own copy of these numbers):
 
     AND=0  OR=1  NOT=2  EQ=3  NOISY_IMPLY=4  NOISY_AND=5  PRIOR=6
+    TERMS=7  (generic: the factor's local structure is an explicit term list)
 """
 from __future__ import annotations
 
@@ -22,8 +23,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-AND, OR, NOT, EQ, NOISY_IMPLY, NOISY_AND, PRIOR = range(7)
-TYPE_NAMES = ("AND", "OR", "NOT", "EQ", "NOISY_IMPLY", "NOISY_AND", "PRIOR")
+AND, OR, NOT, EQ, NOISY_IMPLY, NOISY_AND, PRIOR, TERMS = range(8)
+TYPE_NAMES = ("AND", "OR", "NOT", "EQ", "NOISY_IMPLY", "NOISY_AND", "PRIOR", "TERMS")
 
 
 @dataclass
@@ -36,6 +37,10 @@ class FactorGraph:
     factor_param float32[A]    p for NOISY_IMPLY / NOISY_AND / PRIOR, else 0
     prior_p1     float32[V]    prior P(x=1) or NaN for no prior
     evidence     int8   [V]    -1 none, 0 or 1 clamped value
+    terms        optional (term_ptr int64 [A+1], term_ind int8, term_w float64):
+                 the term lists of the TERMS factors (others have none); factor
+                 a's indicators are a (terms x variables) block, term after
+                 term, values 0 / 1 / -1 (free), blocks in factor order
     """
 
     n_vars: int
@@ -47,6 +52,7 @@ class FactorGraph:
     evidence: np.ndarray
     name: str = "graph"
     meta: dict = field(default_factory=dict)
+    terms: tuple | None = None
 
     @property
     def n_factors(self) -> int:
@@ -416,6 +422,49 @@ def random_loopy(n_vars: int, n_factors: int, seed: int, max_fan: int = 5,
     ev[m] = rng.integers(0, 2, size=int(m.sum())).astype(np.int8)
     return FactorGraph(n_vars, ptr, fv, np.array(ts, np.uint8), np.array(ps, np.float32),
                        prior, ev, f"loopy{n_vars}x{n_factors}_s{seed}")
+
+
+def random_terms(rng: np.random.Generator, b: int, max_terms: int = 6, free: float = 0.3,
+                 floor: float = 0.0):
+    """A random term list for a factor over b variables: 1..max_terms terms,
+    each variable fixed to 0 or 1 or left free (probability `free`), weights
+    U(0.1, 1); with floor > 0 a last all-free term of that weight keeps every
+    assignment possible.  Returns (indicators [l, b] int8, weights [l] float64)."""
+    l = int(rng.integers(1, max_terms + 1))
+    ind = rng.integers(0, 2, size=(l, b)).astype(np.int8)
+    ind[rng.random((l, b)) < free] = -1
+    w = rng.uniform(0.1, 1.0, size=l)
+    if floor > 0:
+        ind = np.concatenate([ind, np.full((1, b), -1, np.int8)])
+        w = np.concatenate([w, [floor]])
+    return ind, w
+
+
+def with_generic_factors(g: FactorGraph, frac: float, seed: int, max_terms: int = 6,
+                         free: float = 0.3, floor: float = 0.05) -> FactorGraph:
+    """A copy of g in which a random fraction of the factors (those of at
+    most 32 variables) are replaced by TERMS factors over the same variables
+    with random term lists (random_terms with the given floor)."""
+    rng = np.random.default_rng(seed)
+    ft = np.array(g.factor_type, copy=True)
+    fp = np.asarray(g.factor_ptr)
+    n = np.diff(fp)
+    pick = (rng.random(ft.shape[0]) < frac) & (n <= 32)
+    ft[pick] = TERMS
+    tp = np.zeros(ft.shape[0] + 1, np.int64)
+    inds, ws = [], []
+    for a in range(ft.shape[0]):
+        if ft[a] == TERMS:
+            ind, w = random_terms(rng, int(n[a]), max_terms, free, floor)
+            inds.append(ind.reshape(-1))
+            ws.append(w)
+            tp[a + 1] = tp[a] + w.shape[0]
+        else:
+            tp[a + 1] = tp[a]
+    ti = np.concatenate(inds) if inds else np.zeros(0, np.int8)
+    tw = np.concatenate(ws) if ws else np.zeros(0, np.float64)
+    return FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, ft, g.factor_param, g.prior_p1, g.evidence,
+                       g.name + f"_generic{frac:g}", dict(g.meta), (tp, ti, tw))
 
 
 def fig1_example() -> FactorGraph:

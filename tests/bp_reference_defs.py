@@ -2,7 +2,9 @@
 
 - `factor_table`: the factor function f_a of each logical type as a dense
   table over all assignments, from the type's logical meaning (the readings of
-  the noisy types are stated with each).
+  the noisy types are stated with each); `terms_table`: the table of a generic
+  factor given as an explicit term list (each term a sub-factor that is w_t on
+  the assignments it matches and 0 elsewhere, Eq. 4).
 - `brute_force_marginals`: exact marginals by enumerating every assignment of
   a small graph (the quantity BP reproduces exactly on trees, Sec. 3.2).
 - `sync_bp` / `seq_bp`: textbook synchronous and round-robin sequential BP on
@@ -18,7 +20,7 @@ import itertools
 
 import numpy as np
 
-AND, OR, NOT, EQ, NOISY_IMPLY, NOISY_AND, PRIOR = range(7)
+AND, OR, NOT, EQ, NOISY_IMPLY, NOISY_AND, PRIOR, TERMS = range(8)
 
 
 def factor_value(ftype: int, p: float, x: tuple) -> float:
@@ -52,6 +54,27 @@ def factor_table(ftype: int, p: float, b: int) -> np.ndarray:
     for x in itertools.product((0, 1), repeat=b):
         t[x] = factor_value(ftype, p, x)
     return t
+
+
+def terms_table(ind: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """f(x) = sum over terms t of w_t [x matches t], where term t fixes
+    variable j to ind[t, j] in {0, 1} or leaves it free (-1)."""
+    l, b = ind.shape
+    t = np.zeros((2,) * b)
+    for x in itertools.product((0, 1), repeat=b):
+        t[x] = sum(w[k] for k in range(l) if all(ind[k, j] < 0 or ind[k, j] == x[j] for j in range(b)))
+    return t
+
+
+def table_of(g, a: int) -> np.ndarray:
+    """Dense table of factor a of graph g (typed, or generic with its terms)."""
+    b = int(g.factor_ptr[a + 1] - g.factor_ptr[a])
+    if int(g.factor_type[a]) == TERMS:
+        tp, ti, tw = g.terms
+        off = int(sum((tp[k + 1] - tp[k]) * (g.factor_ptr[k + 1] - g.factor_ptr[k]) for k in range(a)))
+        l = int(tp[a + 1] - tp[a])
+        return terms_table(np.asarray(ti[off:off + l * b]).reshape(l, b), np.asarray(tw[tp[a]:tp[a + 1]]))
+    return factor_table(int(g.factor_type[a]), float(g.factor_param[a]), b)
 
 
 def dense_message(table: np.ndarray, mu: np.ndarray, v: int) -> np.ndarray:
@@ -91,7 +114,7 @@ def brute_force_marginals(g) -> tuple[np.ndarray, float]:
         w *= ph[X[:, v]]
     for a in range(g.n_factors):
         row = g.factor_vars[g.factor_ptr[a]:g.factor_ptr[a + 1]]
-        tab = factor_table(int(g.factor_type[a]), float(g.factor_param[a]), len(row))
+        tab = table_of(g, a)
         w *= tab[tuple(X[:, int(v)] for v in row)]
     Z = w.sum()
     return (w[:, None] * X).sum(0) / Z if Z > 0 else np.full(n, np.nan), Z
@@ -99,8 +122,7 @@ def brute_force_marginals(g) -> tuple[np.ndarray, float]:
 
 def _structures(g):
     rows = [g.factor_vars[g.factor_ptr[a]:g.factor_ptr[a + 1]].tolist() for a in range(g.n_factors)]
-    tabs = [factor_table(int(g.factor_type[a]), float(g.factor_param[a]), len(rows[a]))
-            for a in range(g.n_factors)]
+    tabs = [table_of(g, a) for a in range(g.n_factors)]
     nbrs = {v: [] for v in range(g.n_vars)}
     for a, r in enumerate(rows):
         for v in r:

@@ -404,3 +404,71 @@ def test_invalid_graphs_rejected():
     bad2.factor_vars[0] = 7
     with pytest.raises(ValueError):
         O.Oracle(bad2)
+
+
+# ---------------------------------------------------------------------------
+# Generic factors: local structure given explicitly as a term list (the
+# indicator array of Sec. 4.3.2), evaluated by Algorithm 1.
+# ---------------------------------------------------------------------------
+def test_generic_terms_algorithm1_equals_dense_table():
+    """Random term lists with free variables: Algorithm 1 on the list equals
+    Eq. (2) on the dense table the list defines."""
+    rng = np.random.default_rng(60)
+    for _ in range(40):
+        b = int(rng.integers(1, 7))
+        ind, w = gen.random_terms(rng, b, max_terms=7, free=0.35)
+        tab = R.terms_table(ind, w)
+        mu = rng.uniform(0.0, 1.0, size=(b, 2))
+        oind = np.where(ind.T < 0, -1, ind.T).astype(np.int8)  # oracle layout [b, l]
+        for v in range(b):
+            got = np.array([O.alg1(oind, w, mu, v, 0), O.alg1(oind, w, mu, v, 1)])
+            np.testing.assert_allclose(got, R.dense_message(tab, mu, v), rtol=1e-13, atol=1e-15)
+
+
+def test_generic_factor_with_a_types_terms_equals_the_type():
+    """A TERMS factor carrying a typed factor's own term list gives the same
+    BP messages as the typed factor."""
+    for s in range(3):
+        g = gen.random_tree(12, seed=610 + s)
+        fp = np.asarray(g.factor_ptr)
+        tp = [0]
+        inds, ws = [], []
+        for a in range(g.n_factors):
+            b = int(fp[a + 1] - fp[a])
+            ind, w = O.terms(int(g.factor_type[a]), b, float(g.factor_param[a]))
+            inds.append(ind.T.reshape(-1))  # [l, b], term after term
+            ws.append(w)
+            tp.append(tp[-1] + w.shape[0])
+        h = gen.FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, np.full(g.n_factors, gen.TERMS, np.uint8),
+                            g.factor_param, g.prior_p1, g.evidence, g.name + "_asterms", {},
+                            (np.array(tp, np.int64), np.concatenate(inds).astype(np.int8), np.concatenate(ws)))
+        a = O.Oracle(g).run("PARALL", 20, 0.0)
+        b_ = O.Oracle(h).run("PARALL", 20, 0.0)
+        np.testing.assert_array_equal(a["a2v"], b_["a2v"])
+
+
+def test_generic_bp_exact_on_trees():
+    """On trees with generic factors (random term lists), BP marginals equal
+    brute-force exact marginals."""
+    checked = 0
+    for s in range(8):
+        g = gen.with_generic_factors(gen.random_tree(int(8 + s % 7), seed=620 + s), 0.6, seed=630 + s)
+        exact, Z = R.brute_force_marginals(g)
+        if not Z > 0:
+            continue
+        o = O.Oracle(g)
+        res = o.run("PARALL", max_iters=200, tol=1e-15)
+        np.testing.assert_allclose(o.marginals(res["a2v"]), exact, atol=1e-12, err_msg=g.name)
+        checked += 1
+    assert checked >= 6
+
+
+def test_generic_terms_rejected_when_malformed():
+    g = gen.with_generic_factors(gen.random_loopy(10, 8, seed=640), 1.0, seed=641)
+    tp, ti, tw = g.terms
+    bad = [(tp, np.where(ti == 0, 2, ti).astype(np.int8), tw), (tp, ti, -tw)]
+    for terms in bad:
+        h = gen.FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, g.factor_type, g.factor_param,
+                            g.prior_p1, g.evidence, "bad", {}, terms)
+        with pytest.raises(ValueError):
+            O.Oracle(h)

@@ -57,7 +57,8 @@ extern "C" {
  *      y=1 w.p. p, a false premise leaves y free; PRIOR(p): P(y=1) = p) ---- */
 enum {
     FBP_AND = 0, FBP_OR = 1, FBP_NOT = 2, FBP_EQ = 3,
-    FBP_NOISY_IMPLY = 4, FBP_NOISY_AND = 5, FBP_PRIOR = 6
+    FBP_NOISY_IMPLY = 4, FBP_NOISY_AND = 5, FBP_PRIOR = 6,
+    FBP_TERMS = 7  /* generic: local structure from fbp_set_factor_terms */
 };
 
 /* ---- update strategies (Table 1; Definition 2) -------------------------
@@ -165,6 +166,26 @@ int fbp_schedule_build_host(int32_t n_vars, int32_t n_factors, const int64_t *fa
 /* Clamp variable var to value (0/1), or release it (-1: back to its prior).
  * Used by the serving loop; takes effect at the next fbp_run. */
 int fbp_set_evidence(fbp_graph *g, int32_t var, int8_t value);
+
+/* Local structure of the generic (FBP_TERMS) factors, given explicitly as
+ * the indicator array of Sec. 4.3.2 with a weight per term (Eq. 4): the
+ * factor is the sum of its terms, term t being w_t on the assignments that
+ * agree with its fixed variables and 0 elsewhere; its messages are computed
+ * by Algorithm 1.
+ *   term_ptr [n_factors+1] int64, term_ptr[0] = 0: factor a's terms are
+ *            term_ptr[a] .. term_ptr[a+1]-1 (none for typed factors;
+ *            at most 256 per factor).
+ *   term_ind int8: factor a's indicators are a block of
+ *            (terms of a) x (variables of a) values, term after term, each
+ *            variable in the factor's row order: 0 or 1 (the term fixes the
+ *            variable) or -1 (free); blocks in factor order.
+ *   term_w   [term_ptr[n_factors]] float, finite and >= 0.
+ * Arrays are copied.  A graph with FBP_TERMS factors (at most 32 variables
+ * each) must receive their terms before its first fbp_run, which otherwise
+ * returns FBP_ERR_INVALID_ARG; calling it again replaces them.  Returns
+ * FBP_ERR_INVALID_ARG for a malformed list (the message names the factor). */
+int fbp_set_factor_terms(fbp_graph *g, const int64_t *term_ptr, const int8_t *term_ind,
+                         const float *term_w);
 
 /* Copy the a->v messages out as normalised (m0, m1) pairs, a2v[2E] host, or
  * in (checkpoint / resume; warm start). */

@@ -26,7 +26,8 @@ extern "C" {
 
 /* One graph of a batch (arrays as in fbp_graph_create; borrowed for the
  * duration of fbp_batch_create).  schedule.strategy may be any static
- * strategy or PARALL (RESIDUAL is rejected). */
+ * strategy or PARALL (RESIDUAL is rejected); generic (FBP_TERMS) factors are
+ * rejected (they need fbp_set_factor_terms on a single graph). */
 typedef struct {
     int32_t n_vars, n_factors;
     const int64_t *factor_ptr;

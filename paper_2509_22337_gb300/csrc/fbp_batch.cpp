@@ -310,6 +310,9 @@ extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, 
             return fail(FBP_ERR_INVALID_ARG, "batch graph %d: strategy %d not supported in a batch", i,
                         d.schedule.strategy);
         if (d.max_iters < 0 || !(d.tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "batch graph %d: bad max_iters/tol", i);
+        for (int32_t a = 0; a < d.n_factors; ++a)
+            if (d.factor_type[a] == FBP_TERMS)
+                return fail(FBP_ERR_INVALID_ARG, "batch graph %d: generic (FBP_TERMS) factors are for single graphs", i);
     }
     fbp_batch *b = new fbp_batch();
     b->n = n_graphs;

@@ -241,7 +241,9 @@ __device__ __forceinline__ void run_lane(const Pre<kPre> &s, const EngineArgs &A
         } else {
             const int first = pk & 31, n = (pk >> 5) & 63, type = (pk >> 11) & 7;
             const float p = __int_as_float(s.rec.z);
-            const P2 mu = a2v_unified(type, p, n, lane - first, [&](int j) { return sm[first + j]; });
+            const auto getm = [&](int j) { return sm[first + j]; };
+            const P2 mu = type == kTypeTERMS ? a2v_terms(A.g, __ldg(A.g.efac + q), n, lane - first, getm)
+                                             : a2v_unified(type, p, n, lane - first, getm);
             bool gd = false;
             const float r = enc_fast(mu, gd);
             ng += gd;

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
                                                    const float *__restrict__ v2a, float *__restrict__ a2v, IterCtl ctl)
 {
     if (*(volatile const int *)F.done) return;
+    __shared__ float s_x[256];  // the lanes' incoming messages (generic factors read them here)
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     float d = 0.f;
     unsigned long long ng = 0;
@@ -326,11 +327,11 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
         const int4 wr = __ldg(F.warps + w);  // {first edge, end edge, first factor, end factor}
         const int e = wr.x + lane;
         const bool valid = e < wr.y;
-        int lo = wr.x, n = 1, type = 0;
+        int lo = wr.x, n = 1, type = 0, a = 0;
         float p = 0.f, x = 1.f, old = 1.f;
         bool frozen = false;
         if (valid) {
-            const int a = __ldg(g.efac + e);
+            a = __ldg(g.efac + e);
             lo = __ldg(g.fptr + a);
             n = __ldg(g.fptr + a + 1) - lo;
             type = __ldg(g.ftype + a);
@@ -358,8 +359,12 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
             }
         }
         const float ry = __shfl_sync(0xffffffffu, x, (first + y) & 31);
+        s_x[threadIdx.x] = x;
+        __syncwarp();
         if (valid && !frozen) {
-            const P2 mu = a2v_finish(type, p, i == y, A, dec(ry));
+            const float *wx = s_x + (threadIdx.x & ~31) + first;
+            const P2 mu = type == kTypeTERMS ? a2v_terms(g, a, n, i, [&](int j) { return dec(wx[j]); })
+                                             : a2v_finish(type, p, i == y, A, dec(ry));
             bool gd = false;
             const float r = enc_fast(mu, gd);
             ng += gd;

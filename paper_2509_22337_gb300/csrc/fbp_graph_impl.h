@@ -78,6 +78,9 @@ struct fbp_graph {
     // flood_chunk entries (tunable; see FBP_OPT_FLOOD_*)
     int flood_hub_min = fbp::kFloodMediumMax;
     int flood_chunk = fbp::kFloodHubChunk;
+    // generic factors: present in the graph, and their term lists uploaded
+    bool terms_needed = false;
+    bool terms_set = false;
     // batched union graphs: the batch member of every factor (empty for a
     // single graph); lane records carry it in bits 15.. of their packed word
     std::vector<int32_t> fac_graph;

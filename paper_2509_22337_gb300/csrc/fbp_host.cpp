@@ -339,6 +339,7 @@ int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t 
         case FBP_NOT: ok = n == 2; break;
         case FBP_EQ: ok = n >= 1; break;
         case FBP_PRIOR: ok = n == 1; break;
+        case FBP_TERMS: ok = n >= 1 && n <= kTermsMaxVars; break;
         default: return fail(FBP_ERR_INVALID_ARG, "factor %d: unknown type %d", a, t);
         }
         if (!ok) return fail(FBP_ERR_INVALID_ARG, "factor %d: arity %lld invalid for type %d", a, (long long)n, t);
@@ -456,7 +457,66 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
     if (h.ne == 0) ls.lp = {0};
     g->halves.push_back(std::move(ls));
     g->strategy = FBP_PARALL;
+    for (int32_t a = 0; a < n_factors && !g->terms_needed; ++a) g->terms_needed = factor_type[a] == FBP_TERMS;
     *out = g;
+    return FBP_OK;
+}
+
+extern "C" int fbp_set_factor_terms(fbp_graph *g, const int64_t *term_ptr, const int8_t *term_ind,
+                                    const float *term_w)
+{
+    t_err.clear();
+    if (!g || !term_ptr) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    const HostCSR &h = g->h;
+    if (term_ptr[0] != 0) return fail(FBP_ERR_INVALID_ARG, "term_ptr[0] != 0");
+    std::vector<int32_t> tptr(h.na + 1), tioff(std::max(h.na, 1));
+    int64_t ioff = 0;
+    for (int32_t a = 0; a < h.na; ++a) {
+        const int64_t l = term_ptr[a + 1] - term_ptr[a];
+        const int64_t b = h.fptr[a + 1] - h.fptr[a];
+        if (l < 0) return fail(FBP_ERR_INVALID_ARG, "term_ptr decreases at factor %d", a);
+        if (h.ftype[a] != FBP_TERMS && l != 0)
+            return fail(FBP_ERR_INVALID_ARG, "factor %d is not generic but has terms", a);
+        if (l > kTermsMaxTerms) return fail(FBP_ERR_INVALID_ARG, "factor %d has more than %d terms", a, kTermsMaxTerms);
+        tptr[a] = (int32_t)term_ptr[a];
+        tioff[a] = (int32_t)ioff;
+        ioff += l * b;
+        if (ioff >= ((int64_t)1 << 31)) return fail(FBP_ERR_INVALID_ARG, "term lists too large");
+    }
+    const int64_t nt = term_ptr[h.na];
+    if (nt >= ((int64_t)1 << 31)) return fail(FBP_ERR_INVALID_ARG, "too many terms");
+    tptr[h.na] = (int32_t)nt;
+    if ((nt > 0 && !term_w) || (ioff > 0 && !term_ind)) return fail(FBP_ERR_INVALID_ARG, "NULL term arrays");
+    for (int64_t k = 0; k < ioff; ++k)
+        if (term_ind[k] < -1 || term_ind[k] > 1) return fail(FBP_ERR_INVALID_ARG, "indicator %lld not in {-1,0,1}", (long long)k);
+    for (int64_t t = 0; t < nt; ++t)
+        if (!(term_w[t] >= 0.f) || !std::isfinite(term_w[t])) return fail(FBP_ERR_INVALID_ARG, "term %lld: weight not finite and >= 0", (long long)t);
+    if (g->d.tptr) {  // replacing earlier lists
+        dfree(g, (void *)g->d.tptr);
+        dfree(g, (void *)g->d.tioff);
+        dfree(g, (void *)g->d.tind);
+        dfree(g, (void *)g->d.tw);
+        g->d.tptr = g->d.tioff = nullptr;
+        g->d.tind = nullptr;
+        g->d.tw = nullptr;
+    }
+    int32_t *d_tptr = nullptr, *d_tioff = nullptr;
+    int8_t *d_tind = nullptr;
+    float *d_tw = nullptr;
+    int rc;
+    if ((rc = upload(g, &d_tptr, tptr.data(), tptr.size())) || (rc = upload(g, &d_tioff, tioff.data(), tioff.size())))
+        return rc;
+    // empty lists still get a (never read) one-element buffer
+    if ((rc = ioff > 0 ? upload(g, &d_tind, term_ind, (size_t)ioff) : dalloc_n(g, &d_tind, 1)) ||
+        (rc = nt > 0 ? upload(g, &d_tw, term_w, (size_t)nt) : dalloc_n(g, &d_tw, 1)))
+        return rc;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->d.tptr = d_tptr;
+    g->d.tioff = d_tioff;
+    g->d.tind = d_tind;
+    g->d.tw = d_tw;
+    g->terms_set = true;
+    flood_exec_drop(g);  // captured chunks hold the graph structure by value
     return FBP_OK;
 }
 
@@ -770,6 +830,8 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
 {
     t_err.clear();
     if (!g || max_iters < 0 || !(tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
+    if (g->terms_needed && !g->terms_set)
+        return fail(FBP_ERR_INVALID_ARG, "generic (FBP_TERMS) factors have no terms: call fbp_set_factor_terms");
     const HostCSR &h = g->h;
     g->stats = fbp_stats{};
     for (auto &ls : g->halves) g->stats.levels += (int32_t)ls.lp.size() - 1;

@@ -17,7 +17,9 @@
 namespace fbp {
 
 constexpr int kTypeAND = 0, kTypeOR = 1, kTypeNOT = 2, kTypeEQ = 3, kTypeNOISY_IMPLY = 4,
-              kTypeNOISY_AND = 5, kTypePRIOR = 6;
+              kTypeNOISY_AND = 5, kTypePRIOR = 6, kTypeTERMS = 7;
+constexpr int kTermsMaxVars = 32;    // a generic factor fits one warp
+constexpr int kTermsMaxTerms = 256;
 
 // Number of residual slots one iteration spreads its atomics over.
 constexpr int kResSlots = 64;
@@ -32,6 +34,11 @@ struct DevGraph {
     const int32_t *vptr = nullptr;    // [nv+1] variable-major row offsets
     const int32_t *vedge = nullptr;   // [ne] edge ids of each variable, ascending
     const float *phi = nullptr;       // [nv] unary potential, rho-encoded
+    // generic (TERMS) factors: term lists (other factors have none)
+    const int32_t *tptr = nullptr;    // [na+1] first term of each factor
+    const int32_t *tioff = nullptr;   // [na] offset of each factor's indicator block
+    const int8_t *tind = nullptr;     // indicators, (terms x variables) per factor, -1 = free
+    const float *tw = nullptr;        // [terms] weights
 };
 
 // Per-graph convergence state of a batch of independent graphs run together.

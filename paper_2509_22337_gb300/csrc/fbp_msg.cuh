@@ -170,6 +170,32 @@ __device__ __forceinline__ P2 a2v_unified(int type, float p, int n, int i, GetM 
     return a2v_finish(type, p, false, A, getm(y));
 }
 
+// Algorithm 1 for a generic factor a with n variables, target position i:
+// each term that does not conflict with the target's value adds its weight
+// times, for every other variable, the incoming message at the term's value
+// (the sum of both entries where the term leaves the variable free).  getm(j)
+// yields position j's v->a message scaled so that its larger entry is 1.
+template <class GetM>
+__device__ __forceinline__ P2 a2v_terms(const DevGraph &g, int a, int n, int i, GetM getm)
+{
+    const int t0 = __ldg(g.tptr + a), t1 = __ldg(g.tptr + a + 1);
+    const int8_t *ind = g.tind + __ldg(g.tioff + a);
+    P2 mu{0.f, 0.f};
+    for (int t = t0; t < t1; ++t, ind += n) {
+        float prod = __ldg(g.tw + t);
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const P2 m = getm(j);
+            const int c = __ldg(ind + j);
+            prod *= c < 0 ? m.m0 + m.m1 : (c ? m.m1 : m.m0);
+        }
+        const int ci = __ldg(ind + i);
+        if (ci <= 0) mu.m0 += prod;  // free (-1) or 0: counts toward x_i = 0
+        if (ci != 0) mu.m1 += prod;  // free (-1) or 1: counts toward x_i = 1
+    }
+    return mu;
+}
+
 // Hardware reciprocal approximation (rcp.approx.f32: relative error within a
 // couple of ulp, denormals kept).
 __device__ __forceinline__ float rcp_approx(float x)

@@ -554,6 +554,9 @@ extern "C" int fbp_server_session_open(fbp_server *srv, const fbp_graph_desc *d,
     if (st < FBP_PARALL || st > FBP_CUSTOM_RANK || st == FBP_RESIDUAL)
         return fail(FBP_ERR_INVALID_ARG, "session strategy %d is not PARALL or a static strategy", st);
     if (d->max_iters < 0 || !(d->tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad max_iters or tol");
+    for (int32_t a = 0; a < d->n_factors; ++a)
+        if (d->factor_type[a] == FBP_TERMS)
+            return fail(FBP_ERR_INVALID_ARG, "generic (FBP_TERMS) factors are for single graphs");
     const int64_t ne = d->factor_ptr[d->n_factors];
     if (ne >= ((int64_t)1 << 31)) return fail(FBP_ERR_INVALID_ARG, "graph too large");
     std::unique_ptr<Sess> s(new Sess());

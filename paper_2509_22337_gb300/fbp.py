@@ -20,7 +20,7 @@ from . import build as _build
 
 FBP_OK, FBP_NOT_CONVERGED = 0, 1
 FBP_ERR_INVALID_ARG, FBP_ERR_OOM, FBP_ERR_CUDA, FBP_ERR_SCHEDULE, FBP_ERR_TIMEOUT = -1, -2, -3, -4, -5
-FBP_AND, FBP_OR, FBP_NOT, FBP_EQ, FBP_NOISY_IMPLY, FBP_NOISY_AND, FBP_PRIOR = range(7)
+FBP_AND, FBP_OR, FBP_NOT, FBP_EQ, FBP_NOISY_IMPLY, FBP_NOISY_AND, FBP_PRIOR, FBP_TERMS = range(8)
 FBP_PARALL, FBP_SEQFIX, FBP_TOPO, FBP_TOPO_FB, FBP_RESIDUAL, FBP_CUSTOM_RANK = range(6)
 STRATEGY = dict(PARALL=0, SEQFIX=1, TOPO=2, TOPO_FB=3, RESIDUAL=4, CUSTOM=5, CUSTOM_RANK=5)
 
@@ -82,13 +82,14 @@ def load(path: str | None = None):
         L.fbp_messages_reset.argtypes = [vp]
         L.fbp_set_option.argtypes = [vp, i32, i64]
         L.fbp_run_fixed_scratch.argtypes = [vp, i32, f64, C.POINTER(i32), C.POINTER(f64)]
+        L.fbp_set_factor_terms.argtypes = [vp, vp, vp, vp]
         L.fbp_graph_destroy.argtypes = [vp]
         L.fbp_graph_destroy.restype = None
         L.fbp_last_error.restype = C.c_char_p
         for name in ("fbp_graph_create", "fbp_schedule_set", "fbp_run", "fbp_marginals",
                      "fbp_schedule_levels", "fbp_schedule_build_host", "fbp_set_evidence",
                      "fbp_messages_export", "fbp_messages_import", "fbp_get_stats", "fbp_messages_reset",
-                     "fbp_set_option", "fbp_run_fixed_scratch"):
+                     "fbp_set_option", "fbp_run_fixed_scratch", "fbp_set_factor_terms"):
             getattr(L, name).restype = C.c_int
         _bind_extras(L)
         _lib = L
@@ -249,6 +250,15 @@ def fbp_schedule_build_host(n_vars, n_factors, factor_ptr, factor_vars, strategy
     return lp, le[: int(fp[-1])]
 
 
+def fbp_set_factor_terms(g, term_ptr, term_ind, term_w) -> int:
+    """Term lists of the generic (FBP_TERMS) factors (layout: include/fbp.h)."""
+    tp = np.ascontiguousarray(term_ptr, np.int64)
+    ti = np.ascontiguousarray(term_ind, np.int8)
+    tw = np.ascontiguousarray(term_w, np.float32)
+    return _check(load().fbp_set_factor_terms(g, tp.ctypes.data, ti.ctypes.data if ti.size else None,
+                                              tw.ctypes.data if tw.size else None))
+
+
 def fbp_set_evidence(g, var: int, value: int):
     return _check(load().fbp_set_evidence(g, int(var), int(value)))
 
@@ -295,6 +305,8 @@ class Graph:
         self.n_vars, self.n_edges = int(fg.n_vars), int(fp[-1])
         self.h = fbp_graph_create(fg.n_vars, fp.shape[0] - 1, fp, fv, ft, fpar, pr, ev,
                                   alloc=alloc, stream=stream)
+        if getattr(fg, "terms", None) is not None:
+            fbp_set_factor_terms(self.h, *fg.terms)
         if strategy != "PARALL" or spec:
             fbp_schedule_set(self.h, strategy, **spec)
 

@@ -52,3 +52,18 @@ def test_batch_rejects_bad_member_before_any_device_work(lib):
     assert ei.value.code == F.FBP_ERR_INVALID_ARG and "batch graph 1" in str(ei.value)
     with pytest.raises(F.FbpError):
         B.fbp_batch_create([good], ["RESIDUAL"], [10], [0.0], alloc=None, stream=0)
+
+
+def test_generic_factor_arity_and_batches(lib):
+    """Generic (FBP_TERMS) factors: at most 32 variables; single graphs only."""
+    from paper_2509_22337_gb300 import fbp_batch as B
+    wide = gen.FactorGraph(40, np.array([0, 40], np.int64), np.arange(40, dtype=np.int32),
+                           np.array([gen.TERMS], np.uint8), np.zeros(1, np.float32),
+                           np.full(40, np.nan, np.float32), np.full(40, -1, np.int8))
+    with pytest.raises(F.FbpError) as ei:
+        _create(wide)
+    assert ei.value.code == F.FBP_ERR_INVALID_ARG and "arity" in str(ei.value)
+    g = gen.with_generic_factors(gen.random_loopy(12, 10, seed=650), 0.5, seed=651)
+    with pytest.raises(F.FbpError) as ei:
+        B.fbp_batch_create([g], ["PARALL"], [10], [0.0], alloc=None, stream=0)
+    assert ei.value.code == F.FBP_ERR_INVALID_ARG and "generic" in str(ei.value)

@@ -42,6 +42,10 @@ WORKLOADS = {
                 "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
                 "PARALL to max change < 1e-6 or 500 iterations"),
     "tiny": ("tiny", "PARALL", 50, 0.0, "tiny derivation DAG, PARALL, exactly 50 iterations"),
+    "generic200k": ("generic", "TOPO_FB", 100, 1e-6,
+                    "SmartFL-200k structure with every factor generic: random term lists (1-6 terms, "
+                    "variables free w.p. 0.3, plus a 0.05-weight all-free term) evaluated by Algorithm 1; "
+                    "TOPO_FB to max change < 1e-6 or 100 sweeps"),
     "batched": ("batched", "MIXED", 0, 1e-6,
                 "512 graphs, sizes log-uniform in 1e3..1e5: even SmartFL-shaped (TOPO_FB, tol 1e-6, <= 100 "
                 "sweeps), odd BINGO-shaped (PARALL, tol 1e-6, <= 500 iterations); one batched run"),
@@ -55,6 +59,8 @@ WORKLOADS = {
 def make_graph(name):
     from paper_2509_22337_gb300 import gen
     kind = WORKLOADS[name][0]
+    if kind == "generic":
+        return gen.with_generic_factors(gen.smartfl(), 1.0, seed=9)
     return {"smartfl": gen.smartfl, "bingo": gen.bingo, "tiny": gen.tiny}[kind]()
 
 
@@ -590,7 +596,7 @@ def run_reference(args):
     _, strategy, max_iters, tol, desc = WORKLOADS[args.workload]
     g = make_graph(args.workload)
     o = O.Oracle(g)
-    sample_iters = {"smartfl200k": 4, "bingo1m": 2, "tiny": 50}[args.workload]
+    sample_iters = {"smartfl200k": 4, "bingo1m": 2, "tiny": 50, "generic200k": 2}[args.workload]
     for _ in range(args.warmup):
         o.run(strategy, 1, 0.0)
     times, upd = [], 0

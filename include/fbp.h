@@ -206,7 +206,10 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  * FBP_OPT_ENGINE_GRID  blocks of the persistent level engine in grid mode
  *                      (0 = automatic choice of mode and size).
  * FBP_OPT_ENGINE       1 (default): static strategies run in the persistent
- *                      engine; 0: one launch per level (reference path).
+ *                      engine with a grid barrier between levels; 2: the
+ *                      persistent engine in dataflow form (a lane waits only
+ *                      for the messages it reads from earlier levels; same
+ *                      results); 0: one launch per level (reference path).
  * FBP_OPT_ENGINE_CLUSTER 0 (default): automatic; 1: never run the engine as
  *                      one thread-block cluster; 8 or 16: always, with that
  *                      cluster size.

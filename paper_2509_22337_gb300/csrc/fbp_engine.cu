@@ -35,6 +35,8 @@
 // (ld/st.global.cg); the plan and the graph structure are read-only.
 #include "fbp_msg.cuh"
 
+#include <algorithm>
+
 namespace fbp {
 
 namespace {
@@ -91,8 +93,40 @@ __device__ __forceinline__ int grid_wait(const unsigned *counter, unsigned targe
     return s_fail;
 }
 
+// Dataflow execution (k_engine_df): every message a half writes starts as
+// this NaN, which the encodings never produce; a reader of a message written
+// at an earlier level of the half waits until the value replaces it.  The
+// message is its own flag, so a relaxed load of the one word suffices.
+constexpr unsigned kPending = 0x7fc0dea1u;
+
+__device__ __forceinline__ float ld_relaxed(const float *p)
+{
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// v: a first load of *p.  Waits (bounded by spin_limit cycles) while the
+// message is pending; on expiry raises the error word, which ends the run at
+// its next grid barrier.
+__device__ __forceinline__ float await_msg(const float *p, float v, const EngineArgs &A)
+{
+    if (__float_as_uint(v) != kPending) return v;
+    const long long t0 = clock64();
+    for (int n = 0;; ++n) {
+        v = ld_relaxed(p);
+        if (__float_as_uint(v) != kPending) return v;
+        if (clock64() - t0 > A.spin_limit) {
+            atomicExch(A.out + 2, 1);
+            return 1.f;
+        }
+        if (n > 16) __nanosleep(32);
+    }
+}
+
 // Incoming v->a message of edge q = (a, v) at level L without prefetch (the
 // per-edge path of factors wider than a warp).
+template <bool kDF>
 __device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P, int q, int L,
                                      const float *cur, const float *nxt)
 {
@@ -105,7 +139,10 @@ __device__ __forceinline__ P2 v2a_at(const EngineArgs &A, const LevelPlanDev &P,
             rr[u] = 1.f;
             if (k0 + u < er.y) {
                 const int2 ev = __ldg(P.vel + k0 + u);
-                if (ev.x != q) rr[u] = ev.y < L ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+                if (ev.x != q) {
+                    rr[u] = ev.y < L ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+                    if (kDF && ev.y < L) rr[u] = await_msg(nxt + ev.x, rr[u], A);
+                }
             }
         }
 #pragma unroll
@@ -174,6 +211,53 @@ __device__ __forceinline__ void prefetch_b(Pre<kPre> &s, const PreA &a, const En
     s.kend = er.y;
 }
 
+// The second round split in two for a pipeline two levels deep: the loads
+// (raw row entries and phi), then, a level later, the lane state derived
+// from them, so that no instruction waits on a load issued in the same level.
+template <int kPre>
+struct PreB {
+    int2 ev[kPre];
+    float phi;
+};
+
+template <int kPre>
+__device__ __forceinline__ void prefetch_b_issue(PreB<kPre> &b, const PreA &a, const EngineArgs &A,
+                                                 const LevelPlanDev &P)
+{
+    b.phi = 1.f;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) b.ev[u] = make_int2(-1, 0);
+    if (a.rec.x < 0) return;
+    b.phi = __ldg(A.g.phi + a.rec.w);
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (a.er.x + u < a.er.y) b.ev[u] = __ldg(P.vel + a.er.x + u);
+}
+
+template <int kPre>
+__device__ __forceinline__ void prefetch_b_finish(Pre<kPre> &s, const PreA &a, const PreB<kPre> &b, int La)
+{
+    s.rec = a.rec;
+    s.phi = b.phi;
+    s.use_nxt = 0u;
+    s.live = 0u;
+    s.kmore = a.er.x + kPre;
+    s.kend = a.er.y;
+    if (a.rec.x < 0) {
+        s.kmore = s.kend = 0;
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        s.e[u] = 0;
+        if (a.er.x + u < a.er.y) {
+            s.e[u] = b.ev[u].x;
+            if (b.ev[u].x != a.rec.x) s.live |= 1u << u;
+            if (b.ev[u].y < La) s.use_nxt |= 1u << u;
+        }
+    }
+}
+
 template <int kPre>
 __device__ __forceinline__ void prefetch(Pre<kPre> &s, const EngineArgs &A, const LevelPlanDev &P, int La, int slot,
                                          int s1)
@@ -186,7 +270,7 @@ __device__ __forceinline__ void prefetch(Pre<kPre> &s, const EngineArgs &A, cons
 // One lane's share of a level: its position's v->a product, then (if its edge
 // is in the level) its factor's closed form a->v message.  Called by whole
 // warps (the __syncwarp()s).
-template <int kPre>
+template <int kPre, bool kDF>
 __device__ __forceinline__ void run_lane(const Pre<kPre> &s, const EngineArgs &A, const LevelPlanDev &P, int La,
                                          const float *cur, float *nxt, P2 *sm, float &rmax,
                                          unsigned long long &ng)
@@ -206,6 +290,11 @@ __device__ __forceinline__ void run_lane(const Pre<kPre> &s, const EngineArgs &A
         for (int u = 0; u < kPre; ++u)
             r[u] = ((s.live >> u) & 1u) ? (((s.use_nxt >> u) & 1u) ? __ldcg(nxt + s.e[u]) : __ldcg(cur + s.e[u]))
                                          : 1.f;
+        if (kDF) {  // messages of earlier levels of this half: wait for the pending ones
+#pragma unroll
+            for (int u = 0; u < kPre; ++u)
+                if ((s.live >> u) & (s.use_nxt >> u) & 1u) r[u] = await_msg(nxt + s.e[u], r[u], A);
+        }
         m = dec(s.phi);
 #pragma unroll
         for (int u = 0; u < kPre; ++u) {
@@ -220,7 +309,10 @@ __device__ __forceinline__ void run_lane(const Pre<kPre> &s, const EngineArgs &A
                 rr[u] = 1.f;
                 if (k0 + u < s.kend) {
                     const int2 ev = __ldg(P.vel + k0 + u);
-                    if (ev.x != q) rr[u] = ev.y < La ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+                    if (ev.x != q) {
+                        rr[u] = ev.y < La ? __ldcg(nxt + ev.x) : __ldcg(cur + ev.x);
+                        if (kDF && ev.y < La) rr[u] = await_msg(nxt + ev.x, rr[u], A);
+                    }
                 }
             }
 #pragma unroll
@@ -339,11 +431,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                 }
                 PreA next;
                 prefetch_a(next, Pn, __ldg(Pn.lane_ptr + Ln) + my0, __ldg(Pn.lane_ptr + Ln + 1));
-                run_lane(pre, A, P, La, cur, nxt, sm, rmax, ng);
+                run_lane<kPre, false>(pre, A, P, La, cur, nxt, sm, rmax, ng);
                 for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
                     Pre<kPre> more;
                     prefetch(more, A, P, La, slot, s1);
-                    run_lane(more, A, P, La, cur, nxt, sm, rmax, ng);
+                    run_lane<kPre, false>(more, A, P, La, cur, nxt, sm, rmax, ng);
                 }
                 // factors wider than a warp: one thread per edge
                 const int b0 = __ldg(P.big_ptr + L), b1 = __ldg(P.big_ptr + L + 1);
@@ -352,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                     const int a = __ldg(A.g.efac + e);
                     const int lo = __ldg(A.g.fptr + a), n = __ldg(A.g.fptr + a + 1) - lo;
                     const P2 mu = a2v_unified(__ldg(A.g.ftype + a), __ldg(A.g.fparam + a), n, e - lo,
-                                              [&](int j) { return v2a_at(A, P, lo + j, La, cur, nxt); });
+                                              [&](int j) { return v2a_at<false>(A, P, lo + j, La, cur, nxt); });
                     bool gd = false;
                     const float r = enc_fast(mu, gd);
                     ng += gd;
@@ -421,6 +513,132 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
     }
 }
 
+// The dataflow engine: the same levels and the same arithmetic as k_engine,
+// without a grid barrier between levels.  At the start of a half every
+// message the half writes is set pending (then one grid barrier); a lane
+// waits only for the messages it reads that earlier levels of the half write
+// (await_msg), and reads every other message from the level-start buffer,
+// which nothing writes during the half.  So every lane reads exactly the
+// values the level-by-level execution gives it, and a level starts as soon as
+// its own inputs exist instead of when the slowest lane of the previous level
+// finishes.  A half ends with a grid barrier (all reads of the old buffer
+// done) before the buffers swap.  No wait can deadlock: a lane waits only on
+// lanes of lower levels of the same half, every thread takes its levels in
+// order, and the cooperative launch keeps every block resident.  Every wait
+// is bounded (spin_limit).  Static strategies only (every edge is written
+// once per half).
+template <int kPre>
+__global__ void __launch_bounds__(kBlock, 1) k_engine_df(EngineArgs A)
+{
+    __shared__ P2 s_m[kBlock];
+    P2 *sm = s_m + (threadIdx.x & ~31);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int my0 = gw * 32 + lane;
+    float *cur = A.buf[0], *nxt = A.buf[1];
+    unsigned long long ng = 0;
+    unsigned target = 0;
+    int it, status = 1, failed = 0;
+    const bool empty = A.n_halves == 0 ||
+                       (A.half[0].n_levels == 0 && (A.n_halves < 2 || A.half[1].n_levels == 0));
+    Pre<kPre> pre;
+    for (it = 1; it <= A.max_iters && !failed && !empty; ++it) {
+        float rmax = 0.f;
+        for (int h = 0; h < A.n_halves && !failed; ++h) {
+            const LevelPlanDev P = plan_at(A, h);
+            for (int e = tid; e < A.g.ne; e += nthr) __stcg(nxt + e, __uint_as_float(kPending));
+            // plan pipeline: level L's lane state, level L+1's loads, level L+2's records
+            PreA rec1;
+            PreB<kPre> raw1;
+            if (P.n_levels > 0)
+                prefetch(pre, A, P, P.level_base, __ldg(P.lane_ptr) + my0, __ldg(P.lane_ptr + 1));
+            if (P.n_levels > 1) {
+                prefetch_a(rec1, P, __ldg(P.lane_ptr + 1) + my0, __ldg(P.lane_ptr + 2));
+                prefetch_b_issue(raw1, rec1, A, P);
+            }
+            grid_arrive(A.bar);
+            target += gridDim.x;
+            if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
+                failed = 1;
+                break;
+            }
+            for (int L = 0; L < P.n_levels; ++L) {
+                const int La = L + P.level_base;
+                const int s0 = __ldg(P.lane_ptr + L), s1 = __ldg(P.lane_ptr + L + 1);
+                PreA rec2;
+                if (L + 2 < P.n_levels) prefetch_a(rec2, P, __ldg(P.lane_ptr + L + 2) + my0, __ldg(P.lane_ptr + L + 3));
+                run_lane<kPre, true>(pre, A, P, La, cur, nxt, sm, rmax, ng);
+                for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
+                    Pre<kPre> more;
+                    prefetch(more, A, P, La, slot, s1);
+                    run_lane<kPre, true>(more, A, P, La, cur, nxt, sm, rmax, ng);
+                }
+                const int b0 = __ldg(P.big_ptr + L), b1 = __ldg(P.big_ptr + L + 1);
+                for (int b = b0 + tid; b < b1; b += nthr) {  // factors wider than a warp
+                    const int e = __ldg(P.big + b);
+                    const int a = __ldg(A.g.efac + e);
+                    const int lo = __ldg(A.g.fptr + a), n = __ldg(A.g.fptr + a + 1) - lo;
+                    const P2 mu = a2v_unified(__ldg(A.g.ftype + a), __ldg(A.g.fparam + a), n, e - lo,
+                                              [&](int j) { return v2a_at<true>(A, P, lo + j, La, cur, nxt); });
+                    bool gd = false;
+                    const float r = enc_fast(mu, gd);
+                    ng += gd;
+                    rmax = fmaxf(rmax, delta_p1_fast(r, __ldcg(cur + e)));
+                    __stcg(nxt + e, r);
+                }
+                if (L + 1 < P.n_levels) prefetch_b_finish(pre, rec1, raw1, La + 1);
+                if (L + 2 < P.n_levels) {
+                    prefetch_b_issue(raw1, rec2, A, P);
+                    rec1 = rec2;
+                }
+            }
+            if (h + 1 == A.n_halves) {
+                const float bm = block_max(rmax);
+                if (threadIdx.x == 0 && bm > 0.f) max_bits(A.res + (it - 1), __float_as_uint(bm));
+            }
+            grid_arrive(A.bar);
+            target += gridDim.x;
+            if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
+                failed = 1;
+                break;
+            }
+            float *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        if (failed) break;
+        if (A.batch.n_graphs > 0) {
+            if (blockIdx.x == 0) batch_iteration_end(A.batch, it);
+            grid_arrive(A.bar);
+            target += gridDim.x;
+            if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
+                failed = 1;
+                break;
+            }
+            if (*(volatile int *)A.batch.active == 0) {
+                status = 0;
+                break;
+            }
+            continue;
+        }
+        const float r = __uint_as_float(*(volatile unsigned *)(A.res + (it - 1)));
+        if (r < A.tol) {
+            status = 0;
+            break;
+        }
+    }
+    if (empty) {
+        status = 0;
+        it = 1;
+    }
+    if (ng) atomicAdd(A.guards, ng);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.out[0] = it > A.max_iters ? A.max_iters : it;
+        A.out[1] = failed ? -1 : status;
+    }
+}
+
 }  // namespace
 
 int engine_block() { return kBlock; }
@@ -438,14 +656,16 @@ static int cap_of(const void *kernel)
 int engine_max_grid()
 {
     static int cap = 0;
-    if (!cap) cap = cap_of((const void *)k_engine<false, kBlock, kPreWide>);
+    if (!cap) cap = std::min(cap_of((const void *)k_engine<false, kBlock, kPreWide>),
+                             cap_of((const void *)k_engine_df<kPreWide>));
     return cap;
 }
 
 static int engine_deep_grid()
 {
     static int cap = 0;
-    if (!cap) cap = cap_of((const void *)k_engine<false, kBlock, kPreDeep>);
+    if (!cap) cap = std::min(cap_of((const void *)k_engine<false, kBlock, kPreDeep>),
+                             cap_of((const void *)k_engine_df<kPreDeep>));
     return cap;
 }
 
@@ -505,9 +725,10 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
     // several passes and are throughput bound: the lighter variant, whose
     // grid may hold two blocks per SM.  Both compute the same messages.
     const bool deep = grid <= engine_deep_grid() && (long long)a.max_lanes <= (long long)grid * kBlock;
-    return cudaLaunchCooperativeKernel(deep ? (void *)k_engine<false, kBlock, kPreDeep>
-                                            : (void *)k_engine<false, kBlock, kPreWide>,
-                                       dim3(grid), dim3(kBlock), params, 0, s);
+    const void *kernel = a.dataflow ? (deep ? (const void *)k_engine_df<kPreDeep> : (const void *)k_engine_df<kPreWide>)
+                                    : (deep ? (const void *)k_engine<false, kBlock, kPreDeep>
+                                            : (const void *)k_engine<false, kBlock, kPreWide>);
+    return cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBlock), params, 0, s);
 }
 
 }  // namespace fbp

@@ -710,6 +710,7 @@ EngineArgs engine_args(fbp_graph *g)
     A.out = g->d_out;
     A.spin_limit = g->spin_limit;
     for (auto &ls : g->halves) A.max_lanes = std::max(A.max_lanes, ls.max_lanes);
+    A.dataflow = g->use_engine == 2;
     return A;
 }
 
@@ -795,6 +796,7 @@ int run_per_level(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_ou
             for (int32_t L = 0; L < full.n_levels; ++L) {
                 CUDA_TRY(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 2, g->stream));
                 EngineArgs A = engine_args(g);
+                A.dataflow = 0;
                 LevelPlanDev one = full;
                 one.lane_ptr = full.lane_ptr + L;
                 one.big_ptr = full.big_ptr + L;
@@ -948,6 +950,7 @@ int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters
         A.max_iters = 1;
         A.tol = 0.f;
         A.dres = g->dres;
+        A.dataflow = 0;  // only the active edges are written
         if (n > 0) {
             int grid = 1, cluster = 0;
             engine_shape(g, &grid, &cluster);
@@ -982,7 +985,8 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         g->engine_grid = (int)std::min<int64_t>(value, engine_max_grid());
         return FBP_OK;
     case FBP_OPT_ENGINE:
-        g->use_engine = value != 0;
+        if (value < 0 || value > 2) return fail(FBP_ERR_INVALID_ARG, "FBP_OPT_ENGINE must be 0, 1 or 2");
+        g->use_engine = (int)value;
         return FBP_OK;
     case FBP_OPT_FLOOD_HUB_MIN:
         if (value < kFloodSmallMax || value > kFloodMediumMax)

@@ -80,6 +80,7 @@ struct EngineArgs {
     float tol = 0.f;
     long long spin_limit = 0;          // clock64 cycles one barrier may wait
     int32_t max_lanes = 0;             // widest level of the plans, in lanes (launch shape)
+    int32_t dataflow = 0;              // grid mode: per-message waits instead of a barrier per level
     // batched graphs (n_graphs > 0): every lane record carries its graph in
     // bits 15.. of its packed word; each graph stops on its own residual.
     BatchCtl batch;

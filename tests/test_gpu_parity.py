@@ -354,3 +354,46 @@ def test_engine_prefetch_variants_agree(fbp):
         out.append(G.messages())
         G.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("grid", [0, 5])
+def test_dataflow_engine_equals_barrier_engine(fbp, grid):
+    """The dataflow engine (per-message waits instead of a barrier per level)
+    computes exactly the level engine's messages: several strategies, levels
+    wider than the grid (grid 5), a factor wider than a warp."""
+    wide = gen.FactorGraph(40, np.array([0, 36, 38, 40], np.int64),
+                           np.concatenate([np.arange(36), [36, 37], [38, 39]]).astype(np.int32),
+                           np.array([gen.OR, gen.NOT, gen.AND], np.uint8), np.zeros(3, np.float32),
+                           np.full(40, 0.3, np.float32), np.full(40, -1, np.int8), "wide")
+    cases = [(gen.smartfl(n_layers=20, width=60, seed=770), "TOPO_FB", None),
+             (gen.tiny(), "SEQFIX", None), (gen.tiny(), "TOPO", None),
+             (gen.random_loopy(80, 70, seed=771), "CUSTOM", np.random.default_rng(772)),
+             (wide, "SEQFIX", None)]
+    for g, strat, rng in cases:
+        custom = rng.integers(0, 6, size=g.n_edges).astype(np.int64) if rng is not None else None
+        out = []
+        for mode in (1, 2):
+            G = fbp.Graph(g, strat, edge_rank=custom) if custom is not None else fbp.Graph(g, strat)
+            G.set_option(fbp.FBP_OPT_ENGINE, mode)
+            if grid:
+                G.set_option(fbp.FBP_OPT_ENGINE_GRID, grid)
+            st = G.run(7, 1e-9)
+            out.append((st, G.messages()))
+            G.close()
+        assert out[0][0] == out[1][0], (g.name, strat)
+        assert np.array_equal(out[0][1], out[1][1]), (g.name, strat)
+
+
+def test_dataflow_wait_timeout_is_reported(fbp):
+    g = gen.smartfl(n_layers=10, width=40, seed=773)
+    G = fbp.Graph(g, "TOPO_FB")
+    G.set_option(fbp.FBP_OPT_ENGINE, 2)
+    G.set_option(fbp.FBP_OPT_ENGINE_GRID, 4)
+    G.set_option(fbp.FBP_OPT_SPIN_LIMIT, 0)
+    with pytest.raises(fbp.FbpError) as ei:
+        G.run(3, 0.0)
+    assert ei.value.code == fbp.FBP_ERR_TIMEOUT
+    G.set_option(fbp.FBP_OPT_SPIN_LIMIT, 4_000_000_000)
+    G.reset()
+    assert G.run(3, 0.0)[1] == 3
+    G.close()

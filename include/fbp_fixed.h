@@ -63,8 +63,8 @@ extern "C" {
  *
  * Errors: FBP_ERR_INVALID_ARG for g == NULL, max_iters < 0, max_iters >
  * FBP_FIXED_SCRATCH_MAX_ITERS (the message names the limit), tol < 0 or NaN,
- * or a graph whose strategy is PARALL or RESIDUAL (both need per-run
- * buffers this entry point does not have); FBP_ERR_CUDA when the symbol
+ * a graph whose strategy is PARALL or RESIDUAL (both need per-run buffers
+ * this entry point does not have), or generic factors without their terms; FBP_ERR_CUDA when the symbol
  * lookup or a launch fails; FBP_ERR_TIMEOUT as fbp_run.  Nothing runs and
  * the graph is unchanged when an argument is rejected. */
 int fbp_run_fixed_scratch(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,

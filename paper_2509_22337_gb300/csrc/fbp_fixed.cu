@@ -78,6 +78,8 @@ extern "C" int fbp_run_fixed_scratch(fbp_graph *g, int32_t max_iters, double tol
     if (g->strategy == FBP_PARALL || g->strategy == FBP_RESIDUAL)
         return fail(FBP_ERR_INVALID_ARG, "fbp_run_fixed_scratch needs a static strategy "
                                          "(SEQFIX, TOPO, TOPO_FB or CUSTOM_RANK)");
+    if (g->terms_needed && !g->terms_set)
+        return fail(FBP_ERR_INVALID_ARG, "generic (FBP_TERMS) factors have no terms: call fbp_set_factor_terms");
     unsigned char *base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;

@@ -91,6 +91,11 @@ def test_generic_terms_required_and_validated(fbp):
     with pytest.raises(fbp.FbpError) as ei:
         G.run(3, 0.0)
     assert ei.value.code == fbp.FBP_ERR_INVALID_ARG and "terms" in str(ei.value)
+    S = fbp.Graph(bare, "SEQFIX")
+    with pytest.raises(fbp.FbpError) as ei:
+        S.run_fixed_scratch(3, 0.0)
+    assert ei.value.code == fbp.FBP_ERR_INVALID_ARG and "terms" in str(ei.value)
+    S.close()
     tp, ti, tw = g.terms
     for bad in [(tp, np.where(ti == 1, 3, ti), tw), (tp, ti, -np.asarray(tw)), (tp + 1, ti, tw)]:
         with pytest.raises(fbp.FbpError) as ei:

@@ -41,6 +41,10 @@ WORKLOADS = {
     "bingo1m": ("bingo", "PARALL", 500, 1e-6,
                 "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
                 "PARALL to max change < 1e-6 or 500 iterations"),
+    "bingo1m_residual": ("bingo", "RESIDUAL", 500, 1e-6,
+                         "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
+                         "RESIDUAL (classes and Algorithm 2 levels built on the device every iteration) to max "
+                         "change < 1e-6 or 500 iterations"),
     "tiny": ("tiny", "PARALL", 50, 0.0, "tiny derivation DAG, PARALL, exactly 50 iterations"),
     "generic200k": ("generic", "TOPO_FB", 100, 1e-6,
                     "SmartFL-200k structure with every factor generic: random term lists (1-6 terms, "
@@ -56,9 +60,23 @@ WORKLOADS = {
 }
 
 
-def make_graph(name):
+# Workloads whose full-size graph the oracle cannot run one iteration of in a
+# bounded sample: its Algorithm 2 scan walks every edge of each neighbouring
+# variable, and BINGO's hub variables carry ~1e5 edges (one RESIDUAL iteration
+# of the 1M-tuple graph took 562 s on one core).  The CPU sample then runs the
+# same generator at a smaller scale, and says so.
+ORACLE_SAMPLE_GRAPHS = {
+    "bingo1m_residual": (dict(n_tuples=100_000),
+                         "the same generator at 1/10 scale (100k tuples; this overstates the oracle's full-size "
+                         "rate, as its cost per edge grows with hub degree)"),
+}
+
+
+def make_graph(name, **kw):
     from paper_2509_22337_gb300 import gen
     kind = WORKLOADS[name][0]
+    if kw:
+        return {"smartfl": gen.smartfl, "bingo": gen.bingo, "tiny": gen.tiny}[kind](**kw)
     if kind == "generic":
         return gen.with_generic_factors(gen.smartfl(), 1.0, seed=9)
     return {"smartfl": gen.smartfl, "bingo": gen.bingo, "tiny": gen.tiny}[kind]()
@@ -497,6 +515,14 @@ def run_gpu(args):
         kkey = "flood"
         launches_per_step = max(sweeps, 1)
         bytes_per_launch = algorithmic_bytes_flood(g)
+    elif strategy == "RESIDUAL":
+        # one RESIDUAL iteration: the device schedule, then each of its
+        # levels as a flooding step over the whole graph (bytes of one level:
+        # a lower bound when an iteration has several levels)
+        kname = "RESIDUAL iteration (device schedule + flooding levels)"
+        kkey = "flood"
+        launches_per_step = max(sweeps, 1)
+        bytes_per_launch = algorithmic_bytes_flood(g)
     else:
         kname = "k_engine (persistent level engine, one launch per run)"
         kkey = "k_engine"
@@ -572,7 +598,8 @@ def cpu_baseline(workload, budget_s=15.0, impl_line=False):
     from oracle import oracle as O
     O.build()
     _, strategy, max_iters, tol, _ = WORKLOADS[workload]
-    g = make_graph(workload)
+    kw, note = ORACLE_SAMPLE_GRAPHS.get(workload, ({}, ""))
+    g = make_graph(workload, **kw)
     o = O.Oracle(g)
     # calibrate: one iteration
     t0 = time.perf_counter()
@@ -583,8 +610,9 @@ def cpu_baseline(workload, budget_s=15.0, impl_line=False):
     r = o.run(strategy, iters, 0.0)
     dt = time.perf_counter() - t0
     return {"value": round(r["updates"] / dt, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {strategy} on the "
-                      f"full {workload} graph from uniform messages ({dt:.1f} s, single thread)"}
+            "sample": f"{iters} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {strategy} on "
+                      + (f"{note}, {g.n_edges} edges," if note else f"the full {workload} graph")
+                      + f" from uniform messages ({dt:.1f} s, single thread)"}
 
 
 def run_reference(args):
@@ -594,9 +622,12 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     _, strategy, max_iters, tol, desc = WORKLOADS[args.workload]
-    g = make_graph(args.workload)
+    kw, note = ORACLE_SAMPLE_GRAPHS.get(args.workload, ({}, ""))
+    g = make_graph(args.workload, **kw)
     o = O.Oracle(g)
-    sample_iters = {"smartfl200k": 4, "bingo1m": 2, "tiny": 50, "generic200k": 2}[args.workload]
+    sample_iters = {"smartfl200k": 4, "bingo1m": 2, "bingo1m_residual": 1, "tiny": 50,
+                    "generic200k": 2}[args.workload]
+    where = f"{note}, {g.n_edges} edges," if note else "the full graph"
     for _ in range(args.warmup):
         o.run(strategy, 1, 0.0)
     times, upd = [], 0
@@ -612,10 +643,11 @@ def run_reference(args):
         "unit": "msg_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "n_vars": g.n_vars, "n_edges": g.n_edges,
-                   "strategy": strategy, "sample": f"{sample_iters} sweeps per step"},
+        "config": {"workload": args.workload, "desc": desc, "strategy": strategy,
+                   "sample": f"{sample_iters} sweeps of {where} per step",
+                   "sample_n_vars": g.n_vars, "sample_n_edges": g.n_edges},
         "cpu_baseline": {"value": round(value, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample_iters} {strategy} sweeps of the full graph per step"},
+                         "sample": f"{sample_iters} {strategy} sweeps of {where} per step"},
         "e2e": {"value": round(value, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

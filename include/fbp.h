@@ -216,10 +216,14 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  * FBP_OPT_FLOOD_HUB_MIN  flooding: variables with more incident factors than
  *                      this (8..256, default 256) are split over blocks.
  * FBP_OPT_FLOOD_CHUNK  flooding: entries of such a variable per block
- *                      (64..65536, default 1024). */
+ *                      (64..65536, default 1024).
+ * FBP_OPT_RESIDUAL_DEVICE 1 (default): RESIDUAL builds each iteration's
+ *                      classes and Algorithm 2 levels on the device and runs
+ *                      the levels with the flooding kernels; 0: classes and
+ *                      levels on the host, levels run by the level engine. */
 enum {
     FBP_OPT_SPIN_LIMIT = 1, FBP_OPT_ENGINE_GRID = 2, FBP_OPT_ENGINE = 3, FBP_OPT_ENGINE_CLUSTER = 4,
-    FBP_OPT_FLOOD_HUB_MIN = 5, FBP_OPT_FLOOD_CHUNK = 6
+    FBP_OPT_FLOOD_HUB_MIN = 5, FBP_OPT_FLOOD_CHUNK = 6, FBP_OPT_RESIDUAL_DEVICE = 7
 };
 int fbp_set_option(fbp_graph *g, int32_t option, int64_t value);
 

@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
         const float ry = __shfl_sync(0xffffffffu, x, (first + y) & 31);
         s_x[threadIdx.x] = x;
         __syncwarp();
-        if (valid && !frozen) {
+        const bool write = valid && !frozen && (!F.elevel || __ldg(F.elevel + e) == F.level);
+        if (write) {
             const float *wx = s_x + (threadIdx.x & ~31) + first;
             const P2 mu = type == kTypeTERMS ? a2v_terms(g, a, n, i, [&](int j) { return dec(wx[j]); })
                                              : a2v_finish(type, p, i == y, A, dec(ry));
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
             ng += gd;
             d = delta_p1_fast(r, old);
             a2v[e] = r;
+            if (F.dres) F.dres[e] = d;
         }
     }
     if (ng) atomicAdd(ctl.guards, ng);
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodP
             graph = __ldg(F.fgraph + a);
             frozen = __ldcg(F.batch.done + graph) != 0;
         }
-        if (!frozen) {
+        if (!frozen && (!F.elevel || __ldg(F.elevel + e) == F.level)) {
             const P2 mu = a2v_unified(__ldg(g.ftype + a), __ldg(g.fparam + a), n, e - lo,
                                       [&](int j) { return dec(__ldg(v2a + lo + j)); });
             bool gd = false;
@@ -408,6 +410,7 @@ __global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodP
             ng += gd;
             d = delta_p1_fast(r, a2v[e]);
             a2v[e] = r;
+            if (F.dres) F.dres[e] = d;
         }
     }
     if (ng) atomicAdd(ctl.guards, ng);
@@ -490,6 +493,24 @@ void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float
     if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, v2a, a2v, ctl);
     if (P.batch.n_graphs > 0) k_flood_batch_check<<<1, 1024, 0, s>>>(P.batch, done);
     else k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, tol, done);
+}
+
+void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, int *done,
+                 cudaStream_t s)
+{
+    FloodPlanDev P = F;
+    P.done = done;
+    if (g.nv > 0) k_v2a_lean<<<(g.nv + 255) / 256, 256, 0, s>>>(g, P, a2v, v2a);
+    if (P.n_hub > 0) k_hub_partials<<<P.n_hub, 256, 0, s>>>(g, P, a2v);
+    const int nb = P.nb_small + P.nb_medium + P.n_hub;
+    if (nb > 0) k_v2a_rest<<<nb, 256, 0, s>>>(g, P, a2v, v2a);
+    if (P.n_warps > 0) k_a2v_lanes<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+    if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+}
+
+void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t s)
+{
+    k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, tol, done);
 }
 
 cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,

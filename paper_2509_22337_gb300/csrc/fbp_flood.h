@@ -36,6 +36,12 @@ struct FloodPlanDev {
     int32_t n_wide = 0;
     const int32_t *wide = nullptr;     // [n_wide] edges of factors wider than a warp
     const int *done = nullptr;         // set once the run has converged
+    // one level of the device-scheduled RESIDUAL strategy: phase 2 writes only
+    // the edges with elevel[e] == level, and records each written edge's
+    // |dP(x=1)| in dres (unused when elevel is null)
+    const int8_t *elevel = nullptr;
+    int32_t level = 0;
+    float *dres = nullptr;
     // batched graphs: graph of each variable and factor; per-graph state
     const int32_t *vgraph = nullptr;
     const int32_t *fgraph = nullptr;
@@ -54,6 +60,13 @@ struct FloodPlanDev {
 // iteration.
 void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
                      unsigned *hist, int *done, cudaStream_t s);
+// The two phases of one level of a device-scheduled RESIDUAL iteration
+// (F.elevel, F.level, F.dres set): every v->a message from the level-start
+// state, then the level's a->v messages.  No convergence check.
+void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, int *done,
+                 cudaStream_t s);
+// End of a device-scheduled RESIDUAL iteration: the check of flood_iteration.
+void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t s);
 // A CUDA graph of `iters` consecutive flood_iterations (captured on a private
 // stream; launch it on any stream).
 cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,

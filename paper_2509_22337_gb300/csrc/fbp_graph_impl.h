@@ -9,6 +9,7 @@
 #include "fbp_flood.h"
 #include "fbp_internal.h"
 #include "fbp_sched.h"
+#include "fbp_residual.h"
 
 using fbp::DevGraph;
 using fbp::FloodPlanDev;
@@ -78,6 +79,10 @@ struct fbp_graph {
     // flood_chunk entries (tunable; see FBP_OPT_FLOOD_*)
     int flood_hub_min = fbp::kFloodMediumMax;
     int flood_chunk = fbp::kFloodHubChunk;
+    // RESIDUAL: schedule built on the device (default) or on the host
+    bool residual_device = true;
+    fbp::ResidualWork rs;
+    bool rs_levels_pending = false;   // the last device iteration's levels are not on the host yet
     // generic factors: present in the graph, and their term lists uploaded
     bool terms_needed = false;
     bool terms_set = false;
@@ -123,6 +128,7 @@ int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_
 // tolerance tol (captured again when any of them, the message buffer or the
 // residual words changed).
 int flood_exec_for(fbp_graph *g, const FloodPlanDev &F, float tol, int iters, cudaGraphExec_t *out);
+int fetch_residual_levels(fbp_graph *g);
 void flood_exec_drop(fbp_graph *g);
 
 }  // namespace fbp

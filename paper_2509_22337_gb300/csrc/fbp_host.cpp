@@ -10,6 +10,7 @@
 #include "fbp_graph_impl.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -523,6 +524,7 @@ extern "C" int fbp_set_factor_terms(fbp_graph *g, const int64_t *term_ptr, const
 extern "C" int fbp_schedule_set(fbp_graph *g, const fbp_schedule_spec *spec)
 {
     t_err.clear();
+    if (g) g->rs_levels_pending = false;
     if (!g || !spec) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
     const HostCSR &h = g->h;
     std::vector<LevelSet> halves;
@@ -603,6 +605,10 @@ extern "C" int fbp_schedule_levels(const fbp_graph *g, int32_t *n_levels, int64_
 {
     t_err.clear();
     if (!g || !n_levels) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
+    if (g->rs_levels_pending && g->strategy == FBP_RESIDUAL) {  // the last device-scheduled RESIDUAL iteration's levels
+        int rc = fetch_residual_levels(const_cast<fbp_graph *>(g));
+        if (rc) return rc;
+    }
     int32_t k = 0;
     for (auto &ls : g->halves) k += (int32_t)ls.lp.size() - 1;
     *n_levels = k;
@@ -839,7 +845,9 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     for (auto &ls : g->halves) g->stats.levels += (int32_t)ls.lp.size() - 1;
     CUDA_TRY(cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), g->stream));
     CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
-    if (g->strategy == FBP_RESIDUAL) return fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
+    if (g->strategy == FBP_RESIDUAL)
+        return g->residual_device ? fbp_run_residual_device(g, max_iters, tol, iters_out, residual_out)
+                                  : fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
     if (g->strategy != FBP_PARALL)
         return g->use_engine ? run_engine(g, max_iters, tol, iters_out, residual_out)
                              : run_per_level(g, max_iters, tol, iters_out, residual_out);
@@ -902,6 +910,112 @@ void fbp::flood_exec_drop(fbp_graph *g)
     if (g->flood_exec) cudaGraphExecDestroy(g->flood_exec);
     g->flood_exec = nullptr;
     g->flood_exec_iters = 0;
+}
+
+// RESIDUAL strategy with the schedule on the device: iteration 1 is one
+// flooding iteration; every later iteration derives the classes and the
+// Algorithm 2 levels from the previous iteration's per-edge changes on the
+// device (residual_schedule) and runs each level as a flooding step that
+// writes only that level's edges (v->a messages from the level-start state,
+// as the level execution prescribes).  Stops at the first iteration whose
+// residual is below tol, or when no factor is active.
+int fbp_run_residual_device(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                            double *residual_out)
+{
+    const HostCSR &h = g->h;
+    int rc;
+    if (!g->v2a && (rc = dalloc_n(g, &g->v2a, (size_t)h.ne))) return rc;
+    if (!g->flood_ready && (rc = build_flood_plan(g))) return rc;
+    if ((rc = ensure_res_cap(g, std::max(max_iters, 1)))) return rc;
+    if (!g->dres && (rc = dalloc_n(g, &g->dres, (size_t)std::max(h.ne, 1)))) return rc;
+    if (!g->rs.ctl) {
+        if ((rc = dalloc_n(g, &g->rs.vres, (size_t)std::max(h.nv, 1))) || (rc = dalloc_n(g, &g->rs.cnt, (size_t)std::max(h.nv, 1))) ||
+            (rc = dalloc_n(g, &g->rs.fcls, (size_t)std::max(h.na, 1))) ||
+            (rc = dalloc_n(g, &g->rs.elev, (size_t)std::max(h.ne, 1))) || (rc = dalloc_n(g, &g->rs.ctl, 4)))
+            return rc;
+    }
+    CUDA_TRY(cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(max_iters, 1), g->stream));
+    if (max_iters == 0) return finish_run(g, 0, 0.0, FBP_NOT_CONVERGED, iters_out, residual_out);
+    CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
+    g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
+    g->h_out[3] = max_iters;
+    CUDA_TRY(cudaMemcpyAsync(g->d_out, g->h_out, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, g->stream));
+    IterCtl ctl{g->d_res, g->d_guards};
+    FloodPlanDev F = g->flood;
+    F.dres = g->dres;
+    const int per_level = flood_launches(g->d, g->flood) - 1;
+    int32_t it = 0, levels = 0;
+    bool idle = false;  // no factor active
+    int status = FBP_NOT_CONVERGED;
+    for (it = 1; it <= max_iters; ++it) {
+        int64_t active = h.ne;
+        levels = 1;
+        if (it == 1) {
+            F.elevel = nullptr;
+        } else {
+            residual_schedule(g->d, g->dres, tol, g->rs, g->stream);
+            g->stats.kernel_launches += 7;
+            CUDA_TRY(cudaMemcpyAsync(g->h_res, g->rs.ctl, sizeof(int) * 4, cudaMemcpyDeviceToHost, g->stream));
+            CUDA_TRY(cudaStreamSynchronize(g->stream));
+            const int *c = reinterpret_cast<const int *>(g->h_res);
+            active = c[kRsActive];
+            levels = 1 + (c[kRsCut1] != INT_MAX) + (c[kRsCut2] != INT_MAX);
+            g->rs_levels_pending = true;
+            if (active == 0) {  // nothing changed by tol or more: the fixed point is reached
+                idle = true;
+                levels = 0;
+                break;
+            }
+            F.elevel = g->rs.elev;
+        }
+        CUDA_TRY(cudaMemsetAsync(g->dres, 0, sizeof(float) * h.ne, g->stream));
+        for (int32_t lv = 0; lv < levels; ++lv) {
+            F.level = lv;
+            flood_level(g->d, F, g->a2v[g->cur], g->v2a, ctl, g->d_out, g->stream);
+            g->stats.kernel_launches += per_level;
+        }
+        flood_check(ctl, (float)tol, g->d_res_it, g->d_out, g->stream);
+        g->stats.kernel_launches += 1;
+        g->stats.updates += active;
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(g->h_out, g->d_out, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        if (g->h_out[0] != 0) break;
+    }
+    if (it > max_iters) it = max_iters;
+    double res = 0.0;
+    if (idle) {
+        status = FBP_OK;
+    } else {
+        it = g->h_out[1];
+        status = g->h_out[0] == 1 ? FBP_OK : FBP_NOT_CONVERGED;
+        res = residual_at(g, it);
+    }
+    g->stats.levels = levels;
+    return finish_run(g, it, res, status, iters_out, residual_out);
+}
+
+// The last device-scheduled RESIDUAL iteration's levels, on the host
+// (canonical order: class, then edge id), for fbp_schedule_levels.
+int fbp::fetch_residual_levels(fbp_graph *g)
+{
+    const HostCSR &h = g->h;
+    std::vector<int8_t> fcls(h.na), elev(h.ne);
+    CUDA_TRY(cudaMemcpyAsync(fcls.data(), g->rs.fcls, h.na, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(elev.data(), g->rs.elev, h.ne, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    LevelSet &ls = g->halves[0];
+    ls.le.clear();
+    for (int c = 0; c <= 2; ++c)
+        for (int32_t e = 0; e < h.ne; ++e)
+            if (fcls[h.efac[e]] == c) ls.le.push_back(e);
+    ls.lp.assign(1, 0);
+    for (size_t i = 0; i < ls.le.size(); ++i)
+        if (i > 0 && elev[ls.le[i]] != elev[ls.le[i - 1]]) ls.lp.push_back((int64_t)i);
+    ls.lp.push_back((int64_t)ls.le.size());
+    if (ls.le.empty()) ls.lp.assign(1, 0);
+    g->rs_levels_pending = false;
+    return FBP_OK;
 }
 
 // RESIDUAL strategy: the classes of the next iteration come from the previous
@@ -983,6 +1097,9 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
     case FBP_OPT_ENGINE_GRID:
         if (value < 0) return fail(FBP_ERR_INVALID_ARG, "negative grid");
         g->engine_grid = (int)std::min<int64_t>(value, engine_max_grid());
+        return FBP_OK;
+    case FBP_OPT_RESIDUAL_DEVICE:
+        g->residual_device = value != 0;
         return FBP_OK;
     case FBP_OPT_ENGINE:
         if (value < 0 || value > 2) return fail(FBP_ERR_INVALID_ARG, "FBP_OPT_ENGINE must be 0, 1 or 2");

@@ -45,5 +45,7 @@ int64_t residual_classes(const HostCSR &h, const float *dres, double tol, int64_
 }  // namespace fbp
 
 struct fbp_graph;
+int fbp_run_residual_device(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
+                            double *residual_out);
 int fbp_run_residual(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
                      double *residual_out);

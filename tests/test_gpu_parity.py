@@ -317,11 +317,12 @@ def test_engine_cluster_mode_does_not_change_results(fbp, cluster):
         assert np.array_equal(a, b), (g.name, cluster)
 
 
-def test_residual_reaches_the_oracles_fixed_points(fbp):
+@pytest.mark.parametrize("device_schedule", [1, 0])
+def test_residual_reaches_the_oracles_fixed_points(fbp, device_schedule):
     """RESIDUAL's levels come from float residuals, so only its outcome is
     compared: the GPU run converges where the FP64 oracle's RESIDUAL run
     does, and its marginals match both the oracle's RESIDUAL and flooding
-    fixed points within 1e-5."""
+    fixed points within 1e-5 (schedule built on the device, or on the host)."""
     graphs = [gen.random_tree(14, seed=500 + s) for s in range(4)]
     graphs += [gen.smartfl(n_layers=12, width=40, seed=31, planted=True),
                gen.random_loopy(60, 50, seed=510)]
@@ -333,7 +334,11 @@ def test_residual_reaches_the_oracles_fixed_points(fbp):
             continue
         if not (in_fp32_range(b_res) and in_fp32_range(b_par)):
             continue
-        a = gpu_run(fbp, g, "RESIDUAL", 400, 1e-7)
+        G = fbp.Graph(g, "RESIDUAL")
+        G.set_option(fbp.FBP_OPT_RESIDUAL_DEVICE, device_schedule)
+        status, it, res = G.run(400, 1e-7)
+        a = dict(status=status, iters=it, residual=res, p=G.marginals().astype(np.float64), stats=G.stats())
+        G.close()
         assert a["status"] == fbp.FBP_OK, (g.name, a["iters"], a["residual"])
         assert np.abs(a["p"] - b_res["p"]).max() <= TOL_P, g.name
         assert np.abs(a["p"] - b_par["p"]).max() <= TOL_P, g.name
@@ -397,3 +402,39 @@ def test_dataflow_wait_timeout_is_reported(fbp):
     G.reset()
     assert G.run(3, 0.0)[1] == 3
     G.close()
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-6])
+def test_residual_device_levels_equal_oracle_algorithm2(fbp, tol):
+    """The device-built RESIDUAL levels of iteration 2 equal the oracle's
+    Algorithm 2 over the same classes: the classes follow from iteration 1's
+    changes (recomputed here from the exported messages; cases whose changes
+    sit within rounding of a class bound are skipped)."""
+    checked = 0
+    for s_ in range(4):
+        g = gen.smartfl(n_layers=8, width=30, seed=780 + s_) if s_ % 2 else gen.bingo(n_tuples=400, seed=780 + s_)
+        G1 = fbp.Graph(g, "RESIDUAL")
+        G1.run(1, 0.0)
+        m = G1.messages().astype(np.float64)
+        G1.close()
+        d = np.abs(m[:, 1] / (m[:, 0] + m[:, 1]) - 0.5)  # change from the uniform start
+        bounds = [b for b in (1e-2, 1e-4, tol) if b > 0]
+        if any(np.any(np.abs(d - b) <= 1e-6 * b) for b in bounds):
+            continue
+        fv = np.asarray(g.factor_vars)
+        fp = np.asarray(g.factor_ptr)
+        vres = np.zeros(g.n_vars)
+        np.maximum.at(vres, fv, d)
+        rank = np.full(g.n_edges, -1, np.int64)
+        for a in range(g.n_factors):
+            rho = vres[fv[fp[a]:fp[a + 1]]].max()
+            rank[fp[a]:fp[a + 1]] = 0 if rho >= 1e-2 else 1 if rho >= 1e-4 else 2 if rho >= tol else -1
+        edges = np.flatnonzero(rank >= 0).astype(np.int64)
+        lp_o, le_o = O.Oracle(g).levels(rank, edges)
+        G2 = fbp.Graph(g, "RESIDUAL")
+        G2.run(2, tol)
+        lp_g, le_g = G2.levels()
+        G2.close()
+        assert np.array_equal(lp_g, lp_o) and np.array_equal(le_g, le_o), g.name
+        checked += 1
+    assert checked >= 2

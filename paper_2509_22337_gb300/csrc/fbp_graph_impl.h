@@ -114,7 +114,9 @@ int upload(fbp_graph *g, T **p, const T *src, size_t n)
 }
 void free_levels_one(fbp_graph *g, LevelSet &ls);
 void free_levels(fbp_graph *g);
-int upload_levels(fbp_graph *g, LevelSet &ls);
+// Upload a level list's engine plan: `packed` when given (pack_levels of the
+// same list), else packed here.
+int upload_levels(fbp_graph *g, LevelSet &ls, const fbp::LevelPack *packed = nullptr);
 int build_flood_plan(fbp_graph *g);
 int ensure_res_cap(fbp_graph *g, int32_t n);
 LevelPlanDev plan_of(const LevelSet &ls);

@@ -16,7 +16,9 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace fbp;
@@ -126,79 +128,23 @@ void free_levels(fbp_graph *g)
 // lrow; idle lanes have edge -1.  Factors wider than a warp
 // go to a per-edge list.  vel[k] pairs the k-th var-major edge with its level
 // (INT_MAX if the edge is in no level: inactive under the residual strategy).
-int upload_levels(fbp_graph *g, LevelSet &ls)
+int upload_levels(fbp_graph *g, LevelSet &ls, const LevelPack *packed)
 {
-    const HostCSR &h = g->h;
-    const int32_t nl = (int32_t)ls.lp.size() - 1;
-    std::vector<int4> lanes;
-    std::vector<int2> lrow;
-    std::vector<int32_t> lane_ptr(1, 0), big, big_ptr(1, 0);
-    std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max());
-    std::vector<int64_t> stamp(h.na, -1);
-    std::vector<uint32_t> fmask(h.na, 0);
-    std::vector<int32_t> order;
-    const int maxfan = engine_max_fan();
-    int32_t max_lanes = 0;
-    for (int32_t L = 0; L < nl; ++L) {
-        order.clear();
-        for (int64_t i = ls.lp[L]; i < ls.lp[L + 1]; ++i) {
-            const int32_t e = ls.le[i];
-            elev[e] = L;
-            const int32_t a = h.efac[e];
-            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
-            if (n > maxfan) {
-                big.push_back(e);
-                continue;
-            }
-            if (stamp[a] != L) {
-                stamp[a] = L;
-                fmask[a] = 0;
-                order.push_back(a);
-            }
-            fmask[a] |= 1u << (e - lo);
-        }
-        const size_t base = lanes.size();
-        int used = 32;  // lanes used in the current warp
-        for (int32_t a : order) {
-            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
-            if (used + n > 32) {
-                while (lanes.size() % 32) {
-                    lanes.push_back(make_int4(-1, 0, 0, 0));
-                    lrow.push_back(make_int2(0, 0));
-                }
-                used = 0;
-            }
-            int32_t pb;
-            std::memcpy(&pb, &h.fparam[a], sizeof pb);
-            for (int32_t j = 0; j < n; ++j) {
-                const int32_t member = g->fac_graph.empty() ? 0 : g->fac_graph[a];
-                const int32_t pk = used | (n << 5) | ((int32_t)h.ftype[a] << 11) |
-                                   ((int32_t)((fmask[a] >> j) & 1u) << 14) | (member << 15);
-                const int32_t v = h.fvars[lo + j];
-                lanes.push_back(make_int4(lo + j, pk, pb, v));
-                lrow.push_back(make_int2(h.vptr[v], h.vptr[v + 1]));
-            }
-            used += n;
-        }
-        while (lanes.size() % 32) {
-            lanes.push_back(make_int4(-1, 0, 0, 0));
-            lrow.push_back(make_int2(0, 0));
-        }
-        max_lanes = std::max(max_lanes, (int32_t)(lanes.size() - base));
-        lane_ptr.push_back((int32_t)lanes.size());
-        big_ptr.push_back((int32_t)big.size());
+    LevelPack local;
+    if (!packed) {
+        pack_levels(g->h, g->fac_graph, ls.lp, ls.le, engine_max_fan(), local);
+        packed = &local;
     }
-    std::vector<int2> vel(h.ne);
-    for (int32_t k = 0; k < h.ne; ++k) vel[k] = make_int2(h.vedge[k], elev[h.vedge[k]]);
+    const LevelPack &P = *packed;
     free_levels_one(g, ls);
-    int rc = upload(g, &ls.d_lanes, lanes.data(), lanes.size());
-    if (!rc) rc = upload(g, &ls.d_lrow, lrow.data(), lrow.size());
-    if (!rc) rc = upload(g, &ls.d_lane_ptr, lane_ptr.data(), lane_ptr.size());
-    if (!rc) rc = upload(g, &ls.d_big, big.data(), big.size());
-    if (!rc) rc = upload(g, &ls.d_big_ptr, big_ptr.data(), big_ptr.size());
-    if (!rc) rc = upload(g, &ls.d_vel, vel.data(), vel.size());
-    ls.max_lanes = max_lanes;
-    ls.n_lanes = (int64_t)lanes.size();
+    int rc = upload(g, &ls.d_lanes, P.lanes.data(), P.lanes.size());
+    if (!rc) rc = upload(g, &ls.d_lrow, P.lrow.data(), P.lrow.size());
+    if (!rc) rc = upload(g, &ls.d_lane_ptr, P.lane_ptr.data(), P.lane_ptr.size());
+    if (!rc) rc = upload(g, &ls.d_big, P.big.data(), P.big.size());
+    if (!rc) rc = upload(g, &ls.d_big_ptr, P.big_ptr.data(), P.big_ptr.size());
+    if (!rc) rc = upload(g, &ls.d_vel, P.vel.data(), P.vel.size());
+    ls.max_lanes = P.max_lanes;
+    ls.n_lanes = (int64_t)P.lanes.size();
     return rc;
 }
 
@@ -536,21 +482,61 @@ extern "C" int fbp_schedule_set(fbp_graph *g, const fbp_schedule_spec *spec)
         ls.lp = {0, (int64_t)h.ne};
         if (h.ne == 0) ls.lp = {0};
         halves.push_back(std::move(ls));
+    } else if (s == FBP_PARALL) {
+        LevelSet ls;  // one class: Algorithm 2 cannot cut, every edge in one level
+        ls.lp = {0, (int64_t)h.ne};
+        if (h.ne == 0) ls.lp = {0};
+        halves.push_back(std::move(ls));
     } else {
-        int nh = s == FBP_TOPO_FB ? 2 : 1;
-        for (int b = 0; b < nh; ++b) {
-            std::vector<int64_t> rank;
-            int rc = build_ranks(h, *spec, b, rank);
-            if (rc) return rc;
-            LevelSet ls;
-            dependency_levels(h, rank.data(), nullptr, h.ne, ls.lp, ls.le);
-            halves.push_back(std::move(ls));
+        const int nh = s == FBP_TOPO_FB ? 2 : 1;
+        std::vector<int64_t> rank[2];
+        int rc = build_ranks(h, *spec, 0, rank[0]);
+        if (rc) return rc;
+        if (nh == 2) backward_ranks(rank[0], rank[1]);
+        halves.resize(nh);
+        std::vector<LevelPack> packs(nh);
+        const int max_fan = engine_max_fan();
+        auto half_work = [&](int b) {
+            dependency_levels(h, rank[b].data(), nullptr, h.ne, halves[b].lp, halves[b].le);
+            pack_levels(h, g->fac_graph, halves[b].lp, halves[b].le, max_fan, packs[b]);
+        };
+        // the two halves of TOPO_FB are independent: the backward one on a
+        // second host thread
+        bool spawned_ok = true;
+        std::thread second;
+        if (nh == 2) {
+            try {
+                second = std::thread([&] {
+                    try {
+                        half_work(1);
+                    } catch (...) {
+                        spawned_ok = false;
+                    }
+                });
+            } catch (...) {
+                half_work(1);  // no thread to be had: run it here
+            }
         }
+        try {
+            half_work(0);
+        } catch (...) {
+            if (second.joinable()) second.join();
+            return fail(FBP_ERR_OOM, "host memory exhausted while building the schedule");
+        }
+        if (second.joinable()) second.join();
+        if (!spawned_ok) return fail(FBP_ERR_OOM, "host memory exhausted while building the schedule");
+        free_levels(g);
+        g->halves = std::move(halves);
+        g->strategy = s;
+        for (int b = 0; b < nh; ++b)
+            if ((rc = upload_levels(g, g->halves[b], &packs[b]))) return rc;
+        if (!g->a2v[1] && dalloc_n(g, &g->a2v[1], (size_t)h.ne)) return FBP_ERR_OOM;
+        return FBP_OK;
     }
     free_levels(g);
     g->halves = std::move(halves);
     g->strategy = s;
-    if (s != FBP_PARALL) {
+    if (s == FBP_RESIDUAL) {
         for (auto &ls : g->halves) {
             if (ls.le.empty() && h.ne) {  // PARALL list (RESIDUAL's first iteration)
                 ls.le.resize(h.ne);
@@ -588,12 +574,19 @@ extern "C" int fbp_schedule_build_host(int32_t n_vars, int32_t n_factors, const 
     std::vector<uint8_t> t(n_factors, 0);
     std::vector<float> p(n_factors, 0.f);
     build_host_csr(n_vars, n_factors, factor_ptr, factor_vars, t.data(), p.data(), h);
-    std::vector<int64_t> rank;
-    int rc = build_ranks(h, *spec, backward ? 1 : 0, rank);
-    if (rc) return rc;
     std::vector<int64_t> lp;
     std::vector<int32_t> le;
-    dependency_levels(h, rank.data(), nullptr, h.ne, lp, le);
+    if (spec->strategy == FBP_PARALL) {
+        lp = {0, (int64_t)h.ne};
+        if (h.ne == 0) lp = {0};
+        le.resize(h.ne);
+        std::iota(le.begin(), le.end(), 0);
+    } else {
+        std::vector<int64_t> rank;
+        int rc = build_ranks(h, *spec, backward ? 1 : 0, rank);
+        if (rc) return rc;
+        dependency_levels(h, rank.data(), nullptr, h.ne, lp, le);
+    }
     *n_levels = (int32_t)(lp.size() - 1);
     if (level_ptr) std::copy(lp.begin(), lp.end(), level_ptr);
     if (level_edges) std::copy(le.begin(), le.end(), level_edges);

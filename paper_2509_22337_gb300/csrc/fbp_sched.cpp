@@ -2,6 +2,7 @@
 #include "fbp_sched.h"
 
 #include <algorithm>
+#include <cstring>
 #include <limits>
 #include <numeric>
 
@@ -65,6 +66,14 @@ static bool variable_depths(const HostCSR &h, std::vector<int64_t> &depth)
     return (int32_t)ready.size() == h.nv;
 }
 
+void backward_ranks(const std::vector<int64_t> &fwd, std::vector<int64_t> &bwd)
+{
+    int64_t mx = 0;
+    for (int64_t r : fwd) mx = std::max(mx, r);
+    bwd.resize(fwd.size());
+    for (size_t e = 0; e < fwd.size(); ++e) bwd[e] = mx - fwd[e];
+}
+
 int build_ranks(const HostCSR &h, const fbp_schedule_spec &spec, int half, std::vector<int64_t> &rank)
 {
     rank.assign(h.ne, 0);
@@ -92,15 +101,51 @@ int build_ranks(const HostCSR &h, const fbp_schedule_spec &spec, int half, std::
             }
         }
         if (half == 1) {
-            int64_t mx = 0;
-            for (int64_t r : rank) mx = std::max(mx, r);
-            for (int64_t &r : rank) r = mx - r;
+            std::vector<int64_t> fwd = std::move(rank);
+            backward_ranks(fwd, rank);
         }
         return FBP_OK;
     }
     default:
         return fail(FBP_ERR_INVALID_ARG, "unknown strategy %d", spec.strategy);
     }
+}
+
+// Canonical order (Definition 2): edges by (rank, edge id).  `edges` (NULL =
+// all edges) lists edge ids in ascending order.  Ranks spanning a range no
+// wider than a few times the edge count (every strategy's but a sparse
+// custom one) are placed by a stable counting sort, which keeps the ascending
+// id order inside each rank; others by a comparison sort of (rank, id) pairs.
+static void canonical_order(const int64_t *rank, const int32_t *edges, int64_t n, std::vector<int32_t> &le)
+{
+    le.resize(n);
+    if (n == 0) return;
+    auto id = [edges](int64_t i) { return edges ? edges[i] : (int32_t)i; };
+    int64_t lo = rank[id(0)], hi = lo;
+    for (int64_t i = 1; i < n; ++i) {
+        const int64_t r = rank[id(i)];
+        lo = std::min(lo, r);
+        hi = std::max(hi, r);
+    }
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;  // exact for hi >= lo
+    if (span <= (uint64_t)(4 * n + 1024)) {
+        std::vector<int64_t> start(span + 2, 0);
+        for (int64_t i = 0; i < n; ++i) ++start[(uint64_t)rank[id(i)] - (uint64_t)lo + 1];
+        for (uint64_t k = 1; k < span + 2; ++k) start[k] += start[k - 1];
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t e = id(i);
+            le[start[(uint64_t)rank[e] - (uint64_t)lo]++] = e;
+        }
+        return;
+    }
+    struct Key {
+        int64_t r;
+        int32_t e;
+    };
+    std::vector<Key> keys(n);
+    for (int64_t i = 0; i < n; ++i) keys[i] = Key{rank[id(i)], id(i)};
+    std::sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) { return x.r != y.r ? x.r < y.r : x.e < y.e; });
+    for (int64_t i = 0; i < n; ++i) le[i] = keys[i].e;
 }
 
 // Algorithm 2 with per-variable counters instead of the scan over NextSet.
@@ -110,21 +155,26 @@ int build_ranks(const HostCSR &h, const fbp_schedule_spec &spec, int half, std::
 // variable v* it suffices to know how many NextSet edges end at v* in total
 // and how many of those belong to the current class; the one edge (a, v*) of
 // factor a itself is discounted.  Counters are reset lazily by stamps (the
-// level index, and a class id that also changes at every cut).
+// level index, and a class id that also changes at every cut).  With a single
+// class nothing can cut, and the edges form one level.
 void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edges, int64_t n,
                        std::vector<int64_t> &lp, std::vector<int32_t> &le)
 {
-    le.resize(n);
-    if (edges) std::copy(edges, edges + n, le.begin());
-    else std::iota(le.begin(), le.end(), 0);
-    std::sort(le.begin(), le.end(), [rank](int32_t x, int32_t y) {
-        return rank[x] != rank[y] ? rank[x] < rank[y] : x < y;
-    });
+    canonical_order(rank, edges, n, le);
     lp.assign(1, 0);
     if (n == 0) return;
-    std::vector<int32_t> cnt_all(h.nv, 0), cnt_cls(h.nv, 0);
-    std::vector<int64_t> st_all(h.nv, -1), st_cls(h.nv, -1);
-    std::vector<int64_t> elev(h.ne, -1);
+    if (rank[le[0]] == rank[le[n - 1]]) {
+        lp.push_back(n);
+        return;
+    }
+    struct VarCount {           // one cache line holds a variable's counters
+        int64_t st_all = -1;    // level of cnt_all
+        int64_t st_cls = -1;    // class of cnt_cls
+        int32_t cnt_all = 0;    // NextSet edges into the variable
+        int32_t cnt_cls = 0;    // ... of the current class
+    };
+    std::vector<VarCount> vc(h.nv);
+    std::vector<int32_t> elev(h.ne, -1);
     int64_t level = 0, cls = 0;
     int64_t cls_rank = rank[le[0]];
     for (int64_t i = 0; i < n; ++i) {
@@ -139,7 +189,8 @@ void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edg
         for (int64_t q = h.fptr[a]; q < h.fptr[a + 1] && !cut; ++q) {
             const int32_t vs = h.fvars[q];
             if (vs == v) continue;
-            int64_t earlier = (st_all[vs] == level ? cnt_all[vs] : 0) - (st_cls[vs] == cls ? cnt_cls[vs] : 0);
+            const VarCount &c = vc[vs];
+            int64_t earlier = (c.st_all == level ? c.cnt_all : 0) - (c.st_cls == cls ? c.cnt_cls : 0);
             if (elev[q] == level && rank[q] < r) --earlier;
             cut = earlier > 0;
         }
@@ -148,13 +199,94 @@ void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edg
             ++level;
             ++cls;
         }
-        elev[e] = level;
-        if (st_all[v] != level) { st_all[v] = level; cnt_all[v] = 0; }
-        ++cnt_all[v];
-        if (st_cls[v] != cls) { st_cls[v] = cls; cnt_cls[v] = 0; }
-        ++cnt_cls[v];
+        elev[e] = (int32_t)level;
+        VarCount &c = vc[v];
+        if (c.st_all != level) { c.st_all = level; c.cnt_all = 0; }
+        ++c.cnt_all;
+        if (c.st_cls != cls) { c.st_cls = cls; c.cnt_cls = 0; }
+        ++c.cnt_cls;
     }
     lp.push_back(n);
+}
+
+static inline int4 i4(int32_t x, int32_t y, int32_t z, int32_t w)
+{
+    int4 r;
+    r.x = x; r.y = y; r.z = z; r.w = w;
+    return r;
+}
+
+static inline int2 i2(int32_t x, int32_t y)
+{
+    int2 r;
+    r.x = x; r.y = y;
+    return r;
+}
+
+void pack_levels(const HostCSR &h, const std::vector<int32_t> &fac_graph, const std::vector<int64_t> &lp,
+                 const std::vector<int32_t> &le, int max_fan, LevelPack &P)
+{
+    const int32_t nl = (int32_t)lp.size() - 1;
+    P = LevelPack{};
+    P.lane_ptr.assign(1, 0);
+    P.big_ptr.assign(1, 0);
+    P.lanes.reserve((size_t)h.ne + (size_t)h.ne / 4 + 32 * (size_t)std::max(nl, 0));
+    P.lrow.reserve(P.lanes.capacity());
+    std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max());
+    std::vector<int32_t> stamp(h.na, -1);
+    std::vector<uint32_t> fmask(h.na, 0);
+    std::vector<int32_t> order;
+    auto pad = [&P] {
+        while (P.lanes.size() % 32) {
+            P.lanes.push_back(i4(-1, 0, 0, 0));
+            P.lrow.push_back(i2(0, 0));
+        }
+    };
+    for (int32_t L = 0; L < nl; ++L) {
+        order.clear();
+        for (int64_t i = lp[L]; i < lp[L + 1]; ++i) {
+            const int32_t e = le.empty() ? (int32_t)i : le[i];
+            elev[e] = L;
+            const int32_t a = h.efac[e];
+            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
+            if (n > max_fan) {
+                P.big.push_back(e);
+                continue;
+            }
+            if (stamp[a] != L) {
+                stamp[a] = L;
+                fmask[a] = 0;
+                order.push_back(a);
+            }
+            fmask[a] |= 1u << (e - lo);
+        }
+        const size_t base = P.lanes.size();
+        int used = 32;  // lanes used in the current warp
+        for (int32_t a : order) {
+            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
+            if (used + n > 32) {
+                pad();
+                used = 0;
+            }
+            int32_t pb;
+            std::memcpy(&pb, &h.fparam[a], sizeof pb);
+            const int32_t member = fac_graph.empty() ? 0 : fac_graph[a];
+            const int32_t common = (n << 5) | ((int32_t)h.ftype[a] << 11) | (member << 15);
+            for (int32_t j = 0; j < n; ++j) {
+                const int32_t pk = used | common | ((int32_t)((fmask[a] >> j) & 1u) << 14);
+                const int32_t v = h.fvars[lo + j];
+                P.lanes.push_back(i4(lo + j, pk, pb, v));
+                P.lrow.push_back(i2(h.vptr[v], h.vptr[v + 1]));
+            }
+            used += n;
+        }
+        pad();
+        P.max_lanes = std::max(P.max_lanes, (int32_t)(P.lanes.size() - base));
+        P.lane_ptr.push_back((int32_t)P.lanes.size());
+        P.big_ptr.push_back((int32_t)P.big.size());
+    }
+    P.vel.resize(h.ne);
+    for (int32_t k = 0; k < h.ne; ++k) P.vel[k] = i2(h.vedge[k], elev[h.vedge[k]]);
 }
 
 int64_t residual_classes(const HostCSR &h, const float *dres, double tol, int64_t *rank,

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <vector>
+#include <vector_types.h>
 
 #include "fbp.h"
 
@@ -30,11 +31,28 @@ void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *
 // Per-edge rank of a static strategy (PARALL, SEQFIX, TOPO, TOPO_FB, CUSTOM_RANK);
 // half = 1 selects the backward half of TOPO_FB.
 int build_ranks(const HostCSR &h, const fbp_schedule_spec &spec, int half, std::vector<int64_t> &rank);
+// TOPO_FB's backward half from the forward ranks: max(0, ranks) - rank.
+void backward_ranks(const std::vector<int64_t> &fwd, std::vector<int64_t> &bwd);
 
 // Algorithm 2 over `edges` (all edges when NULL): canonical (rank, edge id)
 // order, greedy cuts.  lp = level_ptr, le = level_edges.
 void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edges, int64_t n,
                        std::vector<int64_t> &lp, std::vector<int32_t> &le);
+
+// The persistent engine's plan of one level list (host copy): whole factors
+// packed into warps, one lane record per edge {edge, packed word, p bits,
+// variable} and the lane's row bounds; factors wider than max_fan go to the
+// `big` list; vel pairs every variable-major edge with its level.
+struct LevelPack {
+    std::vector<int4> lanes;
+    std::vector<int2> lrow;
+    std::vector<int32_t> lane_ptr, big, big_ptr;
+    std::vector<int2> vel;
+    int32_t max_lanes = 0;
+};
+// fac_graph: batch member of every factor (empty for a single graph).
+void pack_levels(const HostCSR &h, const std::vector<int32_t> &fac_graph, const std::vector<int64_t> &lp,
+                 const std::vector<int32_t> &le, int max_fan, LevelPack &out);
 
 // The residual strategy's classes for the next iteration from the previous
 // iteration's per-edge |delta m1|; fills rank for every edge and the active

@@ -63,15 +63,32 @@ def _graphs():
     yield gen.smartfl(n_layers=200, width=1000, seed=2)
 
 
-@pytest.mark.parametrize("strategy", ["PARALL", "SEQFIX", "TOPO", "TOPO_FB", "CUSTOM"])
+def _custom_ranks(kind, rng, n):
+    """CUSTOM: seven classes (the library places them by counting sort);
+    CUSTOM_WIDE: seven classes spread over +-3 * 2^40 (comparison sort of
+    (rank, id) pairs); CUSTOM_EXTREME: int64 minimum, zero and maximum."""
+    k = rng.integers(0, 7, size=n).astype(np.int64)
+    if kind == "CUSTOM":
+        return k
+    if kind == "CUSTOM_WIDE":
+        return (k - 3) * (np.int64(1) << 40)
+    i64 = np.iinfo(np.int64)
+    return np.choose(k % 3, [np.int64(i64.min), np.int64(0), np.int64(i64.max)]).astype(np.int64)
+
+
+@pytest.mark.parametrize("strategy", ["PARALL", "SEQFIX", "TOPO", "TOPO_FB", "CUSTOM", "CUSTOM_WIDE",
+                                      "CUSTOM_EXTREME"])
 def test_levels_bit_exact_vs_oracle(lib, strategy):
     rng = np.random.default_rng(1)
+    custom_kind = strategy if strategy.startswith("CUSTOM") else None
+    if custom_kind:
+        strategy = "CUSTOM"
     for g in _graphs():
         if g.n_edges > 100000 and strategy in ("SEQFIX", "CUSTOM"):
             continue
         o = O.Oracle(g)
         halves = [False, True] if strategy == "TOPO_FB" else [False]
-        custom = rng.integers(0, 7, size=g.n_edges).astype(np.int64) if strategy == "CUSTOM" else None
+        custom = _custom_ranks(custom_kind, rng, g.n_edges) if custom_kind else None
         for back in halves:
             ostrat = "TOPO" if strategy == "TOPO_FB" else strategy
             try:

@@ -424,6 +424,61 @@ def random_loopy(n_vars: int, n_factors: int, seed: int, max_fan: int = 5,
                        prior, ev, f"loopy{n_vars}x{n_factors}_s{seed}")
 
 
+def hub_and_wide(n_hub: int = 3000, n_medium: int = 200, n_pool: int = 500, seed: int = 71) -> FactorGraph:
+    """Rows and factors at the size boundaries of the kernels' work split: one
+    hub variable in n_hub NOISY_AND(0.9) factors [hub, x, y] (its row spans
+    several 1,024-entry chunks and a ragged tail), one variable in n_medium OR
+    factors [medium, u, z] (a row between 9 and 256 entries), pool variables u
+    of degree ~1-3, and four factors wider than a warp over pool variables: EQ
+    over 40 variables, OR with 34 premises, AND with 33 premises, NOISY_IMPLY(0.95)
+    with 40 premises.  x, y, z and the wide factors' outputs are fresh variables,
+    so no loop runs through the hub and the premise -> output relation is
+    acyclic (every factor has depth 1).  A factor whose output carries no
+    information sends exactly uniform messages to its premises, which would
+    leave the hub's long products untested; the outputs y, z carry priors in
+    U(0.45, 0.55) instead, so every factor sends a mildly informative message
+    and the hub's belief stays away from 0 and 1.  x and pool variables carry
+    priors in U(0.2, 0.8); 2% of the pool is clamped."""
+    rng = np.random.default_rng(seed)
+    hub, medium = 0, 1
+    pool = np.arange(2, 2 + n_pool, dtype=np.int32)
+    nxt = 2 + n_pool
+    rows, ts, ps = [], [], []
+    weak, strong = [], []  # fresh variables with near-1/2 priors / with U(0.2, 0.8) priors
+
+    def fresh(kind: list) -> int:
+        nonlocal nxt
+        nxt += 1
+        kind.append(nxt - 1)
+        return nxt - 1
+
+    for _ in range(n_hub):
+        rows.append(np.array([hub, fresh(strong), fresh(weak)], np.int32))
+        ts.append(NOISY_AND)
+        ps.append(0.9)
+    for _ in range(n_medium):
+        rows.append(np.array([medium, rng.choice(pool), fresh(weak)], np.int32))
+        ts.append(OR)
+        ps.append(0.0)
+    for t, n_prem, p in ((EQ, 39, 0.0), (OR, 34, 0.0), (AND, 33, 0.0), (NOISY_IMPLY, 40, 0.95)):
+        prem = rng.choice(pool, size=n_prem, replace=False).astype(np.int32)
+        rows.append(np.concatenate([prem, np.array([fresh(weak)], np.int32)]))
+        ts.append(t)
+        ps.append(p)
+    ptr, fv = _csr(rows)
+    n_vars = nxt
+    prior = np.full(n_vars, np.nan, dtype=np.float32)
+    prior[pool] = rng.uniform(0.2, 0.8, size=n_pool).astype(np.float32)
+    st, wk = np.array(strong, np.int64), np.array(weak, np.int64)
+    prior[st] = rng.uniform(0.2, 0.8, size=st.size).astype(np.float32)
+    prior[wk] = rng.uniform(0.45, 0.55, size=wk.size).astype(np.float32)
+    ev = np.full(n_vars, -1, dtype=np.int8)
+    clamp = rng.choice(pool, size=max(1, n_pool // 50), replace=False)
+    ev[clamp] = rng.integers(0, 2, size=clamp.size).astype(np.int8)
+    return FactorGraph(n_vars, ptr, fv, np.array(ts, np.uint8), np.array(ps, np.float32), prior, ev,
+                       f"hub{n_hub}_wide_s{seed}")
+
+
 def random_terms(rng: np.random.Generator, b: int, max_terms: int = 6, free: float = 0.3,
                  floor: float = 0.0):
     """A random term list for a factor over b variables: 1..max_terms terms,

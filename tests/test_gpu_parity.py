@@ -127,6 +127,37 @@ def test_small_graphs_all_strategies(fbp, strategy):
     assert checked >= 2
 
 
+@pytest.mark.parametrize("strategy,split", [("PARALL", None), ("PARALL", (9, 64)), ("SEQFIX", None),
+                                            ("TOPO_FB", None)])
+def test_hub_rows_and_wide_factors_vs_oracle(fbp, strategy, split):
+    """A 3,000-entry hub row (three full 1,024-entry chunks and a ragged tail),
+    a 200-entry row, and four factors wider than a warp (40, 35, 34 and 41
+    variables), element by element against the oracle: flooding (hub chunks,
+    warp rows, the wide-factor kernel) and the engine (long rows, the per-edge
+    path of wide factors).  split = (hub_min, chunk) reconfigures the flooding
+    work split so that rows above 9 entries run in 64-entry chunks: the hub in
+    47 chunks with a 56-entry tail, the 200-entry row in 4 with an 8-entry tail."""
+    for seed in (71, 72):
+        g = gen.hub_and_wide(seed=seed)
+        b = oracle_run(g, strategy, 12, 0.0)
+        assert in_fp32_range(b) and b["guards"] == 0
+        G = fbp.Graph(g, strategy)
+        if split:
+            G.set_option(fbp.FBP_OPT_FLOOD_HUB_MIN, split[0])
+            G.set_option(fbp.FBP_OPT_FLOOD_CHUNK, split[1])
+        status, it, res = G.run(12, 0.0)
+        p = G.marginals().astype(np.float64)
+        m = G.messages().astype(np.float64)
+        G.close()
+        assert it == b["iters"] == 12
+        err = np.abs(p - b["p"]).max()
+        assert err <= TOL_P, f"{g.name} {strategy} {split}: max |dp| = {err:.3e}"
+        # the hub's own marginal is a product of 3,000 messages: 1 - p ~ 1e-3..1e-2
+        assert abs(p[0] - b["p"][0]) <= TOL_P
+        print(f"{g.name} {strategy} {split}: max |dp| {err:.2e}, "
+              f"max |d m1| {np.abs(m[:, 1] - b['a2v'][:, 1]).max():.2e}")
+
+
 def test_levels_from_device_graph_match_oracle(fbp):
     g = gen.smartfl(n_layers=30, width=60, seed=31)
     o = O.Oracle(g)
@@ -175,8 +206,14 @@ def test_bingo_1m_sampled_one_step(fbp):
     G.close()
     o = O.Oracle(g)
     rng = np.random.default_rng(5)
-    edges = np.sort(rng.choice(g.n_edges, size=2000, replace=False))
-    # include the edges of the largest hub's first factors
+    edges = rng.choice(g.n_edges, size=2000, replace=False)
+    # and every edge of the first 200 factors of the largest hub: their a->v
+    # messages read the hub's v->a message, a product over ~1e5 entries
+    deg = np.bincount(g.factor_vars, minlength=g.n_vars)
+    hub = int(np.argmax(deg))
+    fac = np.unique(np.searchsorted(g.factor_ptr, np.flatnonzero(g.factor_vars == hub), side="right") - 1)[:200]
+    hub_edges = np.concatenate([np.arange(g.factor_ptr[a], g.factor_ptr[a + 1]) for a in fac])
+    edges = np.unique(np.concatenate([edges, hub_edges]))
     want = o.update_edges(s5, edges)
     assert np.abs(s6[edges, 1] - want[:, 1]).max() <= TOL_P
 

@@ -5,8 +5,47 @@
 #include <cstring>
 #include <limits>
 #include <numeric>
+#include <thread>
 
 namespace fbp {
+
+// Host threads for one schedule build (the two halves of TOPO_FB run their
+// builds side by side).
+static int host_threads()
+{
+    static const int t = [] {
+        const unsigned hw = std::thread::hardware_concurrency();
+        return (int)std::max(1u, std::min(hw / 2, 8u));
+    }();
+    return t;
+}
+
+// body(begin, end) over [0, n) in up to `threads` contiguous parts, the first
+// on the calling thread.  Bodies must not throw (they only write into
+// preallocated arrays).
+template <class Body>
+static void parallel_for(int64_t n, int threads, int64_t min_part, const Body &body)
+{
+    const int64_t parts = std::min<int64_t>(threads, std::max<int64_t>(1, n / std::max<int64_t>(min_part, 1)));
+    if (parts <= 1) {
+        body((int64_t)0, n);
+        return;
+    }
+    const int64_t step = (n + parts - 1) / parts;
+    std::vector<std::thread> pool;
+    pool.reserve(parts - 1);
+    for (int64_t k = 1; k < parts; ++k) {
+        const int64_t b = k * step, e = std::min(n, b + step);
+        if (b >= e) break;
+        try {
+            pool.emplace_back([&body, b, e] { body(b, e); });
+        } catch (...) {  // no thread to be had: run the part here
+            body(b, e);
+        }
+    }
+    body((int64_t)0, std::min(n, step));
+    for (auto &t : pool) t.join();
+}
 
 void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
                     const uint8_t *ftype, const float *fparam, HostCSR &h)
@@ -148,15 +187,17 @@ static void canonical_order(const int64_t *rank, const int32_t *edges, int64_t n
     for (int64_t i = 0; i < n; ++i) le[i] = keys[i].e;
 }
 
-// Algorithm 2 with per-variable counters instead of the scan over NextSet.
-// The cut test for e_i = (a, v) asks whether NextSet holds an edge
-// (a*, v*) with v* in N(a) \ v, a* != a and rank < rank(e_i) (Definition 1).
-// NextSet only holds edges of rank <= rank(e_i) (canonical order), so per
-// variable v* it suffices to know how many NextSet edges end at v* in total
-// and how many of those belong to the current class; the one edge (a, v*) of
-// factor a itself is discounted.  Counters are reset lazily by stamps (the
-// level index, and a class id that also changes at every cut).  With a single
-// class nothing can cut, and the edges form one level.
+// Algorithm 2 (Sec. 4.2.3) without the sequential scan over NextSet.  NextSet
+// is always a contiguous run [s, i) of the canonical order, and e_i = (a, v)
+// ends it exactly when N_E(e_i) (Definition 1) holds an edge of lower rank at a
+// position >= s.  Lower rank means a position before the first edge of e_i's
+// rank class, so with
+//   dep(i) = the largest position p < classStart(i) of an edge (a*, v*) with
+//            v* in N(a) \ v and a* != a
+// (one binary search per variable v* in its positions, sorted) the cut test
+// is dep(i) >= s.  dep is independent per edge and runs on several threads;
+// the cuts follow in one pass.  With a single class nothing can cut, and the
+// edges form one level.
 void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edges, int64_t n,
                        std::vector<int64_t> &lp, std::vector<int32_t> &le)
 {
@@ -167,45 +208,60 @@ void dependency_levels(const HostCSR &h, const int64_t *rank, const int32_t *edg
         lp.push_back(n);
         return;
     }
-    struct VarCount {           // one cache line holds a variable's counters
-        int64_t st_all = -1;    // level of cnt_all
-        int64_t st_cls = -1;    // class of cnt_cls
-        int32_t cnt_all = 0;    // NextSet edges into the variable
-        int32_t cnt_cls = 0;    // ... of the current class
-    };
-    std::vector<VarCount> vc(h.nv);
-    std::vector<int32_t> elev(h.ne, -1);
-    int64_t level = 0, cls = 0;
-    int64_t cls_rank = rank[le[0]];
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t e = le[i];
-        const int64_t r = rank[e];
-        if (r != cls_rank) {
-            cls_rank = r;
-            ++cls;
-        }
-        const int32_t a = h.efac[e], v = h.fvars[e];
-        bool cut = false;
-        for (int64_t q = h.fptr[a]; q < h.fptr[a + 1] && !cut; ++q) {
-            const int32_t vs = h.fvars[q];
-            if (vs == v) continue;
-            const VarCount &c = vc[vs];
-            int64_t earlier = (c.st_all == level ? c.cnt_all : 0) - (c.st_cls == cls ? c.cnt_cls : 0);
-            if (elev[q] == level && rank[q] < r) --earlier;
-            cut = earlier > 0;
-        }
-        if (cut) {
-            lp.push_back(i);
-            ++level;
-            ++cls;
-        }
-        elev[e] = (int32_t)level;
-        VarCount &c = vc[v];
-        if (c.st_all != level) { c.st_all = level; c.cnt_all = 0; }
-        ++c.cnt_all;
-        if (c.st_cls != cls) { c.st_cls = cls; c.cnt_cls = 0; }
-        ++c.cnt_cls;
+    const int T = host_threads();
+    // position of every scheduled edge; -1 for the others
+    std::vector<int32_t> pos(h.ne, -1);
+    parallel_for(n, T, 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) pos[le[i]] = (int32_t)i;
+    });
+    // first position of each position's rank class
+    std::vector<int32_t> cstart(n);
+    cstart[0] = 0;
+    for (int64_t i = 1; i < n; ++i) cstart[i] = rank[le[i]] == rank[le[i - 1]] ? cstart[i - 1] : (int32_t)i;
+    // every variable's scheduled edges as ascending positions
+    std::vector<int32_t> vp(h.nv + 1, 0), vpos(n);
+    if (!edges) {
+        std::copy(h.vptr.begin(), h.vptr.end(), vp.begin());
+    } else {
+        parallel_for(h.nv, T, 1 << 14, [&](int64_t b, int64_t e) {
+            for (int64_t v = b; v < e; ++v) {
+                int32_t c = 0;
+                for (int32_t k = h.vptr[v]; k < h.vptr[v + 1]; ++k) c += pos[h.vedge[k]] >= 0;
+                vp[v + 1] = c;
+            }
+        });
+        for (int32_t v = 0; v < h.nv; ++v) vp[v + 1] += vp[v];
     }
+    parallel_for(h.nv, T, 1 << 14, [&](int64_t b, int64_t e) {
+        for (int64_t v = b; v < e; ++v) {
+            int32_t *out = vpos.data() + vp[v], k = 0;
+            for (int32_t r = h.vptr[v]; r < h.vptr[v + 1]; ++r)
+                if (pos[h.vedge[r]] >= 0) out[k++] = pos[h.vedge[r]];
+            std::sort(out, out + k);
+        }
+    });
+    std::vector<int32_t> dep(n);
+    parallel_for(n, T, 1 << 14, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            const int32_t ei = le[i], a = h.efac[ei], v = h.fvars[ei], cs = cstart[i];
+            int32_t best = -1;
+            for (int64_t q = h.fptr[a]; q < h.fptr[a + 1]; ++q) {
+                const int32_t vs = h.fvars[q];
+                if (vs == v) continue;
+                const int32_t *b0 = vpos.data() + vp[vs], *b1 = vpos.data() + vp[vs + 1];
+                const int32_t *it = std::lower_bound(b0, b1, cs);
+                if (it != b0 && it[-1] == pos[q]) --it;  // a's own edge into vs does not count
+                if (it != b0) best = std::max(best, it[-1]);
+            }
+            dep[i] = best;
+        }
+    });
+    int64_t s0 = 0;  // first position of NextSet
+    for (int64_t i = 0; i < n; ++i)
+        if (dep[i] >= s0) {
+            lp.push_back(i);
+            s0 = i;
+        }
     lp.push_back(n);
 }
 
@@ -227,66 +283,100 @@ void pack_levels(const HostCSR &h, const std::vector<int32_t> &fac_graph, const 
                  const std::vector<int32_t> &le, int max_fan, LevelPack &P)
 {
     const int32_t nl = (int32_t)lp.size() - 1;
+    const int T = host_threads();
     P = LevelPack{};
-    P.lane_ptr.assign(1, 0);
-    P.big_ptr.assign(1, 0);
-    P.lanes.reserve((size_t)h.ne + (size_t)h.ne / 4 + 32 * (size_t)std::max(nl, 0));
-    P.lrow.reserve(P.lanes.capacity());
-    std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max());
-    std::vector<int32_t> stamp(h.na, -1);
-    std::vector<uint32_t> fmask(h.na, 0);
-    std::vector<int32_t> order;
-    auto pad = [&P] {
-        while (P.lanes.size() % 32) {
-            P.lanes.push_back(i4(-1, 0, 0, 0));
-            P.lrow.push_back(i2(0, 0));
-        }
+    auto edge_at = [&le](int64_t i) { return le.empty() ? (int32_t)i : le[i]; };
+    // level and position of every scheduled edge
+    std::vector<int32_t> elev(h.ne, std::numeric_limits<int32_t>::max()), pos(h.ne, -1);
+    parallel_for(nl, T, 16, [&](int64_t b, int64_t e) {
+        for (int64_t L = b; L < e; ++L)
+            for (int64_t i = lp[L]; i < lp[L + 1]; ++i) {
+                elev[edge_at(i)] = (int32_t)L;
+                pos[edge_at(i)] = (int32_t)i;
+            }
+    });
+    // A level's factors are packed in the order of their first edge in the
+    // level, whole factors per warp; an edge is its factor's first in the
+    // level if no other edge of the factor in the level comes earlier.
+    auto first_in_level = [&](int32_t e, int32_t a, int32_t L) {
+        for (int64_t q = h.fptr[a]; q < h.fptr[a + 1]; ++q)
+            if (q != e && elev[q] == L && pos[q] < pos[e]) return false;
+        return true;
     };
+    // pass 1: lanes (whole warps) and wide-factor edges of every level
+    std::vector<int64_t> lanes_at(nl + 1, 0), big_at(nl + 1, 0);
+    parallel_for(nl, T, 16, [&](int64_t b, int64_t e) {
+        for (int64_t L = b; L < e; ++L) {
+            int64_t warps = 0, nbig = 0;
+            int used = 32;
+            for (int64_t i = lp[L]; i < lp[L + 1]; ++i) {
+                const int32_t ed = edge_at(i), a = h.efac[ed];
+                const int n = (int)(h.fptr[a + 1] - h.fptr[a]);
+                if (n > max_fan) {
+                    ++nbig;
+                    continue;
+                }
+                if (!first_in_level(ed, a, (int32_t)L)) continue;
+                if (used + n > 32) {
+                    ++warps;
+                    used = 0;
+                }
+                used += n;
+            }
+            lanes_at[L + 1] = 32 * warps;
+            big_at[L + 1] = nbig;
+        }
+    });
     for (int32_t L = 0; L < nl; ++L) {
-        order.clear();
-        for (int64_t i = lp[L]; i < lp[L + 1]; ++i) {
-            const int32_t e = le.empty() ? (int32_t)i : le[i];
-            elev[e] = L;
-            const int32_t a = h.efac[e];
-            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
-            if (n > max_fan) {
-                P.big.push_back(e);
-                continue;
-            }
-            if (stamp[a] != L) {
-                stamp[a] = L;
-                fmask[a] = 0;
-                order.push_back(a);
-            }
-            fmask[a] |= 1u << (e - lo);
-        }
-        const size_t base = P.lanes.size();
-        int used = 32;  // lanes used in the current warp
-        for (int32_t a : order) {
-            const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
-            if (used + n > 32) {
-                pad();
-                used = 0;
-            }
-            int32_t pb;
-            std::memcpy(&pb, &h.fparam[a], sizeof pb);
-            const int32_t member = fac_graph.empty() ? 0 : fac_graph[a];
-            const int32_t common = (n << 5) | ((int32_t)h.ftype[a] << 11) | (member << 15);
-            for (int32_t j = 0; j < n; ++j) {
-                const int32_t pk = used | common | ((int32_t)((fmask[a] >> j) & 1u) << 14);
-                const int32_t v = h.fvars[lo + j];
-                P.lanes.push_back(i4(lo + j, pk, pb, v));
-                P.lrow.push_back(i2(h.vptr[v], h.vptr[v + 1]));
-            }
-            used += n;
-        }
-        pad();
-        P.max_lanes = std::max(P.max_lanes, (int32_t)(P.lanes.size() - base));
-        P.lane_ptr.push_back((int32_t)P.lanes.size());
-        P.big_ptr.push_back((int32_t)P.big.size());
+        P.max_lanes = std::max(P.max_lanes, (int32_t)lanes_at[L + 1]);
+        lanes_at[L + 1] += lanes_at[L];
+        big_at[L + 1] += big_at[L];
     }
+    P.lanes.assign(lanes_at[nl], int4{-1, 0, 0, 0});
+    P.lrow.assign(lanes_at[nl], int2{0, 0});
+    P.big.resize(big_at[nl]);
+    P.lane_ptr.resize(nl + 1);
+    P.big_ptr.resize(nl + 1);
+    for (int32_t L = 0; L <= nl; ++L) {
+        P.lane_ptr[L] = (int32_t)lanes_at[L];
+        P.big_ptr[L] = (int32_t)big_at[L];
+    }
+    // pass 2: fill every level at its offsets (padding lanes stay {-1, 0, 0, 0})
+    parallel_for(nl, T, 16, [&](int64_t b, int64_t e) {
+        for (int64_t L = b; L < e; ++L) {
+            int64_t w = lanes_at[L] - 32, nb = big_at[L];  // w: first lane of the current warp
+            int used = 32;
+            for (int64_t i = lp[L]; i < lp[L + 1]; ++i) {
+                const int32_t ed = edge_at(i), a = h.efac[ed];
+                const int32_t lo = (int32_t)h.fptr[a], n = (int32_t)(h.fptr[a + 1] - h.fptr[a]);
+                if (n > max_fan) {
+                    P.big[nb++] = ed;
+                    continue;
+                }
+                if (!first_in_level(ed, a, (int32_t)L)) continue;
+                if (used + n > 32) {
+                    w += 32;
+                    used = 0;
+                }
+                uint32_t mask = 0;
+                for (int32_t j = 0; j < n; ++j) mask |= (uint32_t)(elev[lo + j] == (int32_t)L) << j;
+                int32_t pb;
+                std::memcpy(&pb, &h.fparam[a], sizeof pb);
+                const int32_t member = fac_graph.empty() ? 0 : fac_graph[a];
+                const int32_t common = (n << 5) | ((int32_t)h.ftype[a] << 11) | (member << 15);
+                for (int32_t j = 0; j < n; ++j) {
+                    const int32_t v = h.fvars[lo + j];
+                    P.lanes[w + used + j] = i4(lo + j, used | common | ((int32_t)((mask >> j) & 1u) << 14), pb, v);
+                    P.lrow[w + used + j] = i2(h.vptr[v], h.vptr[v + 1]);
+                }
+                used += n;
+            }
+        }
+    });
     P.vel.resize(h.ne);
-    for (int32_t k = 0; k < h.ne; ++k) P.vel[k] = i2(h.vedge[k], elev[h.vedge[k]]);
+    parallel_for(h.ne, T, 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t k = b; k < e; ++k) P.vel[k] = i2(h.vedge[k], elev[h.vedge[k]]);
+    });
 }
 
 int64_t residual_classes(const HostCSR &h, const float *dres, double tol, int64_t *rank,

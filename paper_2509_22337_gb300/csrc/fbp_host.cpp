@@ -10,6 +10,7 @@
 #include "fbp_graph_impl.h"
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -128,8 +129,16 @@ void free_levels(fbp_graph *g)
 // lrow; idle lanes have edge -1.  Factors wider than a warp
 // go to a per-edge list.  vel[k] pairs the k-th var-major edge with its level
 // (INT_MAX if the edge is in no level: inactive under the residual strategy).
+int upload_erow(fbp_graph *g);
+
 int upload_levels(fbp_graph *g, LevelSet &ls, const LevelPack *packed)
 {
+    // the engine's per-edge row records, built with the first level plan (a
+    // graph that only floods never needs them)
+    if (!g->erow && g->h.ne > 0) {
+        int rc = upload_erow(g);
+        if (rc) return rc;
+    }
     LevelPack local;
     if (!packed) {
         pack_levels(g->h, g->fac_graph, ls.lp, ls.le, engine_max_fan(), local);
@@ -153,10 +162,12 @@ int upload_erow(fbp_graph *g)
 {
     const HostCSR &h = g->h;
     std::vector<int4> er(h.ne);
-    for (int32_t e = 0; e < h.ne; ++e) {
-        const int32_t v = h.fvars[e];
-        er[e] = make_int4(h.vptr[v], h.vptr[v + 1], v, 0);
-    }
+    parallel_for(h.ne, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t v = h.fvars[q];
+            er[q] = make_int4(h.vptr[v], h.vptr[v + 1], v, 0);
+        }
+    });
     return upload(g, &g->erow, er.data(), er.size());
 }
 
@@ -256,6 +267,56 @@ int build_flood_plan(fbp_graph *g)
     return FBP_OK;
 }
 
+// One factor's row and type: variables in range and distinct, arity valid for
+// the type, parameter in [0, 1] where the type has one.  With report set, the
+// first problem in row order becomes the thread's error message.
+static int check_factor(int32_t nv, const int64_t *fptr, const int32_t *fvars, const uint8_t *ftype,
+                        const float *fparam, int32_t a, bool report)
+{
+    const int64_t lo = fptr[a], n = fptr[a + 1] - lo;
+    for (int64_t e = lo; e < lo + n; ++e) {
+        const int32_t v = fvars[e];
+        if (v < 0 || v >= nv)
+            return report ? fail(FBP_ERR_INVALID_ARG, "factor %d: variable %d out of range", a, v) : FBP_ERR_INVALID_ARG;
+        if (n <= 64)
+            for (int64_t q = lo; q < e; ++q)
+                if (fvars[q] == v)
+                    return report ? fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, v)
+                                  : FBP_ERR_INVALID_ARG;
+    }
+    if (n > 64) {  // a wide factor: sort a copy; report the first repeat in row order
+        std::vector<int32_t> tmp(fvars + lo, fvars + lo + n);
+        std::sort(tmp.begin(), tmp.end());
+        if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) {
+            if (!report) return FBP_ERR_INVALID_ARG;
+            std::vector<int32_t> seen;
+            for (int64_t e = lo; e < lo + n; ++e) {
+                const auto it = std::lower_bound(seen.begin(), seen.end(), fvars[e]);
+                if (it != seen.end() && *it == fvars[e])
+                    return fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, fvars[e]);
+                seen.insert(it, fvars[e]);
+            }
+        }
+    }
+    const int t = ftype[a];
+    const float p = fparam[a];
+    bool ok;
+    switch (t) {
+    case FBP_AND: case FBP_OR: case FBP_NOISY_IMPLY: case FBP_NOISY_AND: ok = n >= 2; break;
+    case FBP_NOT: ok = n == 2; break;
+    case FBP_EQ: ok = n >= 1; break;
+    case FBP_PRIOR: ok = n == 1; break;
+    case FBP_TERMS: ok = n >= 1 && n <= kTermsMaxVars; break;
+    default: return report ? fail(FBP_ERR_INVALID_ARG, "factor %d: unknown type %d", a, t) : FBP_ERR_INVALID_ARG;
+    }
+    if (!ok)
+        return report ? fail(FBP_ERR_INVALID_ARG, "factor %d: arity %lld invalid for type %d", a, (long long)n, t)
+                      : FBP_ERR_INVALID_ARG;
+    if ((t == FBP_NOISY_IMPLY || t == FBP_NOISY_AND || t == FBP_PRIOR) && !(p >= 0.f && p <= 1.f))
+        return report ? fail(FBP_ERR_INVALID_ARG, "factor %d: parameter outside [0,1]", a) : FBP_ERR_INVALID_ARG;
+    return FBP_OK;
+}
+
 int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
                      const uint8_t *ftype, const float *fparam, const float *prior,
                      const int8_t *evidence)
@@ -269,30 +330,19 @@ int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t 
     if (E >= (int64_t)1 << 31) return fail(FBP_ERR_INVALID_ARG, "too many edges (%lld)", (long long)E);
     if (E > 0 && !fvars) return fail(FBP_ERR_INVALID_ARG, "factor_vars is NULL");
     if (na > 0 && (!ftype || !fparam)) return fail(FBP_ERR_INVALID_ARG, "factor_type/param NULL");
-    std::vector<int32_t> seen((size_t)nv, -1);
-    for (int32_t a = 0; a < na; ++a) {
-        const int64_t lo = fptr[a], n = fptr[a + 1] - lo;
-        for (int64_t e = lo; e < lo + n; ++e) {
-            int32_t v = fvars[e];
-            if (v < 0 || v >= nv) return fail(FBP_ERR_INVALID_ARG, "factor %d: variable %d out of range", a, v);
-            if (seen[v] == a) return fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, v);
-            seen[v] = a;
-        }
-        const int t = ftype[a];
-        const float p = fparam[a];
-        bool ok;
-        switch (t) {
-        case FBP_AND: case FBP_OR: case FBP_NOISY_IMPLY: case FBP_NOISY_AND: ok = n >= 2; break;
-        case FBP_NOT: ok = n == 2; break;
-        case FBP_EQ: ok = n >= 1; break;
-        case FBP_PRIOR: ok = n == 1; break;
-        case FBP_TERMS: ok = n >= 1 && n <= kTermsMaxVars; break;
-        default: return fail(FBP_ERR_INVALID_ARG, "factor %d: unknown type %d", a, t);
-        }
-        if (!ok) return fail(FBP_ERR_INVALID_ARG, "factor %d: arity %lld invalid for type %d", a, (long long)n, t);
-        if ((t == FBP_NOISY_IMPLY || t == FBP_NOISY_AND || t == FBP_PRIOR) && !(p >= 0.f && p <= 1.f))
-            return fail(FBP_ERR_INVALID_ARG, "factor %d: parameter outside [0,1]", a);
-    }
+    // the factors in parallel; the lowest-numbered bad factor is reported
+    std::atomic<int32_t> first_bad{std::numeric_limits<int32_t>::max()};
+    parallel_for(na, host_threads(), 1 << 15, [&](int64_t b, int64_t e) {
+        for (int64_t a = b; a < e && a < first_bad.load(std::memory_order_relaxed); ++a)
+            if (check_factor(nv, fptr, fvars, ftype, fparam, (int32_t)a, false)) {
+                int32_t cur = first_bad.load(std::memory_order_relaxed);
+                while ((int32_t)a < cur && !first_bad.compare_exchange_weak(cur, (int32_t)a)) {
+                }
+                break;
+            }
+    });
+    if (first_bad.load() != std::numeric_limits<int32_t>::max())
+        return check_factor(nv, fptr, fvars, ftype, fparam, first_bad.load(), true);
     if (prior)
         for (int32_t v = 0; v < nv; ++v)
             if (!std::isnan(prior[v]) && !(prior[v] >= 0.f && prior[v] <= 1.f))
@@ -367,7 +417,6 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
         (rc = upload(g, &vptr, h.vptr.data(), h.vptr.size())) ||
         (rc = upload(g, &vedge, h.vedge.data(), h.vedge.size())) ||
         (rc = upload(g, &phi, g->phi.data(), g->phi.size())) ||
-        (rc = upload_erow(g)) ||
         (rc = dalloc_n(g, &g->d_bar, 2)) ||
         (rc = dalloc_n(g, &g->d_out, 4)) ||
         (rc = dalloc_n(g, &g->a2v[0], (size_t)h.ne)) ||

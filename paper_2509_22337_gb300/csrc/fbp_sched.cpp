@@ -9,44 +9,6 @@
 
 namespace fbp {
 
-// Host threads for one schedule build (the two halves of TOPO_FB run their
-// builds side by side).
-static int host_threads()
-{
-    static const int t = [] {
-        const unsigned hw = std::thread::hardware_concurrency();
-        return (int)std::max(1u, std::min(hw / 2, 8u));
-    }();
-    return t;
-}
-
-// body(begin, end) over [0, n) in up to `threads` contiguous parts, the first
-// on the calling thread.  Bodies must not throw (they only write into
-// preallocated arrays).
-template <class Body>
-static void parallel_for(int64_t n, int threads, int64_t min_part, const Body &body)
-{
-    const int64_t parts = std::min<int64_t>(threads, std::max<int64_t>(1, n / std::max<int64_t>(min_part, 1)));
-    if (parts <= 1) {
-        body((int64_t)0, n);
-        return;
-    }
-    const int64_t step = (n + parts - 1) / parts;
-    std::vector<std::thread> pool;
-    pool.reserve(parts - 1);
-    for (int64_t k = 1; k < parts; ++k) {
-        const int64_t b = k * step, e = std::min(n, b + step);
-        if (b >= e) break;
-        try {
-            pool.emplace_back([&body, b, e] { body(b, e); });
-        } catch (...) {  // no thread to be had: run the part here
-            body(b, e);
-        }
-    }
-    body((int64_t)0, std::min(n, step));
-    for (auto &t : pool) t.join();
-}
-
 void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
                     const uint8_t *ftype, const float *fparam, HostCSR &h)
 {

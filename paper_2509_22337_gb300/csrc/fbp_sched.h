@@ -3,13 +3,53 @@
 // (Table 1, Definition 2), and the dependency analysis of Algorithm 2.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
+#include <thread>
 #include <vector>
 #include <vector_types.h>
 
 #include "fbp.h"
 
 namespace fbp {
+
+// Host threads for one parallel host pass (the two halves of TOPO_FB run
+// their schedule builds side by side, each with this many).
+inline int host_threads()
+{
+    static const int t = [] {
+        const unsigned hw = std::thread::hardware_concurrency();
+        return (int)std::max(1u, std::min(hw / 2, 8u));
+    }();
+    return t;
+}
+
+// body(begin, end) over [0, n) in up to `threads` contiguous parts, the first
+// on the calling thread.  Bodies must not throw (they only write into
+// preallocated arrays).
+template <class Body>
+inline void parallel_for(int64_t n, int threads, int64_t min_part, const Body &body)
+{
+    const int64_t parts = std::min<int64_t>(threads, std::max<int64_t>(1, n / std::max<int64_t>(min_part, 1)));
+    if (parts <= 1) {
+        body((int64_t)0, n);
+        return;
+    }
+    const int64_t step = (n + parts - 1) / parts;
+    std::vector<std::thread> pool;
+    pool.reserve(parts - 1);
+    for (int64_t k = 1; k < parts; ++k) {
+        const int64_t b = k * step, e = std::min(n, b + step);
+        if (b >= e) break;
+        try {
+            pool.emplace_back([&body, b, e] { body(b, e); });
+        } catch (...) {  // no thread to be had: run the part here
+            body(b, e);
+        }
+    }
+    body((int64_t)0, std::min(n, step));
+    for (auto &t : pool) t.join();
+}
 
 struct HostCSR {
     int32_t nv = 0, na = 0, ne = 0;

@@ -127,13 +127,14 @@ struct Sess {
 // plans, staging, and the per-iteration residual words.
 int64_t estimate_bytes(int64_t nv, int64_t na, int64_t ne, int32_t max_iters, int strategy)
 {
-    int64_t b = 4 * (na + 1) + 5 * na + 16 * ne /* fvars, efac, vedge, a2v */ + 16 * ne /* erow */ +
+    int64_t b = 4 * (na + 1) + 5 * na + 16 * ne /* fvars, efac, vedge, a2v */ +
                 8 * (nv + 1) /* vptr, phi */ + 4 * nv /* marginals */ + 4 * (int64_t)std::max(max_iters, 64) +
                 (1 << 16);
     if (strategy == FBP_PARALL)
         b += 4 * ne /* v2a */ + 12 * nv /* degree-class lists */ + 64 * (ne / 256 + 1) /* hub chunks */;
     else
-        b += 4 * ne /* second message buffer */ + 2 * (3 * (16 * ne + 8 * ne) / 2 + 8 * ne) /* padded lanes, rows, (edge, level) */ +
+        b += 16 * ne /* the engine's row records */ + 4 * ne /* second message buffer */ +
+             2 * (3 * (16 * ne + 8 * ne) / 2 + 8 * ne) /* padded lanes, rows, (edge, level) */ +
              4 * 8 * ne / 32 /* big lists, level offsets */;
     return b;
 }

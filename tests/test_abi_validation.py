@@ -67,3 +67,33 @@ def test_generic_factor_arity_and_batches(lib):
     with pytest.raises(F.FbpError) as ei:
         B.fbp_batch_create([g], ["PARALL"], [10], [0.0], alloc=None, stream=0)
     assert ei.value.code == F.FBP_ERR_INVALID_ARG and "generic" in str(ei.value)
+
+
+def test_lowest_bad_factor_is_reported(lib):
+    """Factors are checked on several host threads; the error still names the
+    lowest-numbered bad factor, wherever the parts of the range fall."""
+    n = 200_000
+    fp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    fv = np.arange(2 * n, dtype=np.int32) % (n + 1)
+    g = gen.FactorGraph(n + 1, fp, fv, np.full(n, gen.AND, np.uint8), np.zeros(n, np.float32),
+                        np.full(n + 1, np.nan, np.float32), np.full(n + 1, -1, np.int8), "pairs")
+    bad = fv.copy()
+    bad[2 * 150_000 + 1] = n + 7      # factor 150000: variable out of range
+    bad[2 * 40_000 + 1] = bad[2 * 40_000]  # factor 40000: a variable twice
+    with pytest.raises(F.FbpError) as ei:
+        _create(g, factor_vars=bad)
+    assert "factor 40000 lists variable" in str(ei.value)
+
+
+def test_duplicate_in_a_wide_factor_names_the_first_repeat(lib):
+    """A factor wider than 64 variables is checked by sorting a copy; the
+    message names the first variable that repeats in row order."""
+    n = 100
+    row = np.arange(n, dtype=np.int32)
+    row[70] = 5   # repeats variable 5 (first repeat in row order)
+    row[90] = 3   # a later repeat of a smaller variable
+    g = gen.FactorGraph(n, np.array([0, n], np.int64), row, np.array([gen.EQ], np.uint8),
+                        np.zeros(1, np.float32), np.full(n, np.nan, np.float32), np.full(n, -1, np.int8), "wide")
+    with pytest.raises(F.FbpError) as ei:
+        _create(g)
+    assert "lists variable 5 twice" in str(ei.value)

@@ -189,6 +189,20 @@ def algorithmic_bytes_flood(g):
     return 24 * E + 8 * V + 9 * A
 
 
+def pair_model_bytes_per_pass(g):
+    """The method's per-pass byte model, with every message a pair of FP32
+    values (the measure `roofline.achieved` is based on): per edge four
+    message touches of 8 B (gather a->v and write v->a in phase 1, read v->a
+    and write a->v in phase 2) and one 4-B index; per variable its row offset
+    and unary pair (12 B); per factor its row offset, type and parameter
+    (9 B).  One pass is one flooding iteration, or one level list of a static
+    schedule (every edge updated once).  This library stores one float per
+    message, so its own minimum (algorithmic_bytes_flood / _per_half) is
+    lower; both are reported."""
+    E, V, A = g.n_edges, g.n_vars, g.n_factors
+    return 36 * E + 12 * V + 9 * A
+
+
 # Sources each profiled kernel is built from: a DRAM traffic figure taken by
 # ncu is reported only while these files are unchanged.
 KERNEL_SOURCES = {
@@ -372,7 +386,7 @@ def run_serving(args, rank, world, local):
     assert all(i["state"] == SV.FBP_REQ_DONE for i in infos), "a served request failed"
     value = len(infos) / wall
     # algorithmic bytes of every iteration the timed requests ran
-    sess_bytes = [algorithmic_bytes_flood(g) for g in sessions]
+    sess_bytes = [pair_model_bytes_per_pass(g) for g in sessions]
     moved = sum(sess_bytes[i["session"]] * i["iters"] for i in infos)
     peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
@@ -439,7 +453,8 @@ def run_serving(args, rank, world, local):
         "speedup_vs_cold": round(value / (1e3 / float(cold.mean())), 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "flooding iteration kernels of all running requests (24E+8V+9A per iteration)"},
+                     "kernel": "flooding iteration kernels of all running requests",
+                     "bytes_model": "36E+12V+9A per iteration (FP32 message pairs)"},
         "e2e": {"value": round(value, 2), "unit": "req/s", "h2d_bytes_per_step": 4 * per,
                 "d2h_bytes_per_step": int(4 * n_vars_mean * per),
                 "note": "each request is submitted from the host and its marginals land in host memory"},
@@ -526,7 +541,8 @@ def run_gpu(args):
         kname = "flooding iteration (k_v2a_lean, k_hub_partials, k_v2a_rest, k_a2v_lanes, k_flood_check)"
         kkey = "flood"
         launches_per_step = max(sweeps, 1)
-        bytes_per_launch = algorithmic_bytes_flood(g)
+        bytes_per_launch = pair_model_bytes_per_pass(g)
+        layout_bytes = algorithmic_bytes_flood(g)
     elif strategy == "RESIDUAL":
         # one RESIDUAL iteration: the device schedule, then each of its
         # levels as a flooding step over the whole graph (bytes of one level:
@@ -534,12 +550,14 @@ def run_gpu(args):
         kname = "RESIDUAL iteration (device schedule + flooding levels)"
         kkey = "flood"
         launches_per_step = max(sweeps, 1)
-        bytes_per_launch = algorithmic_bytes_flood(g)
+        bytes_per_launch = pair_model_bytes_per_pass(g)
+        layout_bytes = algorithmic_bytes_flood(g)
     else:
         kname = "k_engine (persistent level engine, one launch per run)"
         kkey = "k_engine"
         halves = 2 if strategy == "TOPO_FB" else 1
-        bytes_per_launch = algorithmic_bytes_per_half(g) * halves * sweeps / launches_per_step
+        bytes_per_launch = pair_model_bytes_per_pass(g) * halves * sweeps / launches_per_step
+        layout_bytes = algorithmic_bytes_per_half(g) * halves * sweeps / launches_per_step
     per_launch_ms = kernel_ms / launches_per_step
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0}
@@ -548,6 +566,9 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kkey, args.workload), "kernel": kname,
             "per_launch_us": round(per_launch_ms * 1e3, 3), "bytes_per_launch": int(bytes_per_launch),
+            "bytes_model": "36E+12V+9A per pass (FP32 message pairs)",
+            "bytes_per_launch_layout": int(layout_bytes),
+            "achieved_layout": round(layout_bytes / (per_launch_ms / 1e3) / 1e9, 2),
             "peak_source": "measured" if os.path.exists(peaks_path) else "fallback"}
     levels_per_step = st["levels"] * sweeps
     level_stats = {"levels_per_sweep": st["levels"],

@@ -223,9 +223,11 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
         P2 acc = f;
 #pragma unroll
         for (int u = 0; u < kFloodSmallMax; ++u) {
-            pre[u] = acc;
-            acc = mul(acc, x[u]);
-            resc(acc);
+            if (u < d) {  // the list is sorted by degree, so d is nearly uniform in a warp
+                pre[u] = acc;
+                acc = mul(acc, x[u]);
+                resc(acc);
+            }
         }
         P2 suf{1.f, 1.f};
 #pragma unroll
@@ -248,21 +250,27 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
         const int v = __ldg(F.medium + w);
         if (var_frozen(F, v)) return;
         const int lo = __ldg(g.vptr + v), hi = __ldg(g.vptr + v + 1);
-        // at most kFloodMediumMax / 32 = 8 entries per lane, all loads issued first
+        // at most kFloodMediumMax / 32 = 8 entries per lane, all loads issued
+        // first; ns (uniform in the warp) skips the slots past the row
+        const int ns = (hi - lo + 31) >> 5;
         int e[kFloodMediumMax / 32];
         float r[kFloodMediumMax / 32];
 #pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u) e[u] = lo + lane + 32 * u < hi ? __ldg(g.vedge + lo + lane + 32 * u) : -1;
+        for (int u = 0; u < kFloodMediumMax / 32; ++u) {
+            e[u] = -1;
+            if (u < ns && lo + lane + 32 * u < hi) e[u] = __ldg(g.vedge + lo + lane + 32 * u);
+        }
 #pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u) r[u] = e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
+        for (int u = 0; u < kFloodMediumMax / 32; ++u) r[u] = u < ns && e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
         XP t = xp_one();
 #pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u) xmul(t, r[u]);
+        for (int u = 0; u < kFloodMediumMax / 32; ++u)
+            if (u < ns) xmul(t, r[u]);  // a skipped slot would multiply by exactly 1
         t = warp_product(t);
         const float phi = __ldg(g.phi + v);
 #pragma unroll
         for (int u = 0; u < kFloodMediumMax / 32; ++u)
-            if (e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
+            if (u < ns && e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
         return;
     }
     // hub chunk: combine the row's chunk partials, then every entry of this chunk

@@ -211,6 +211,14 @@ int build_flood_plan(fbp_graph *g)
             hub_n.push_back(nc);
         }
     }
+    // rows of one degree side by side: the per-row loops of a warp then run
+    // to nearly the same length (each row is independent: same results)
+    std::stable_sort(small.begin(), small.end(), [&h](int32_t a, int32_t b) {
+        return h.vptr[a + 1] - h.vptr[a] < h.vptr[b + 1] - h.vptr[b];
+    });
+    std::stable_sort(medium.begin(), medium.end(), [&h](int32_t a, int32_t b) {
+        return h.vptr[a + 1] - h.vptr[a] < h.vptr[b + 1] - h.vptr[b];
+    });
     F.n_small = (int32_t)small.size();
     F.nb_small = (F.n_small + 255) / 256;
     F.n_medium = (int32_t)medium.size();

@@ -105,3 +105,30 @@ def test_generic_terms_required_and_validated(fbp):
     status, it, res = G.run(3, 0.0)
     assert it == 3
     G.close()
+
+
+@pytest.mark.parametrize("device_schedule", [1, 0])
+def test_generic_factors_under_residual(fbp, device_schedule):
+    """Generic factors under RESIDUAL (classes and levels built on the device,
+    or on the host): the run converges and its marginals match the oracle's
+    RESIDUAL and flooding fixed points within 1e-5."""
+    graphs = [gen.with_generic_factors(gen.random_tree(14, seed=730 + s), 0.6, seed=740 + s) for s in range(4)]
+    graphs += [gen.with_generic_factors(gen.smartfl(n_layers=10, width=40, seed=750, planted=True), 0.3, seed=751),
+               gen.with_generic_factors(gen.random_loopy(60, 50, seed=760), 0.5, seed=761)]
+    checked = 0
+    for g in graphs:
+        o = O.Oracle(g)
+        r_res = o.run("RESIDUAL", 400, 1e-7)
+        r_par = o.run("PARALL", 400, 1e-7)
+        if not (r_res["converged"] and r_par["converged"]) or min(r_res["min_pos"], r_par["min_pos"]) < 1e-36:
+            continue
+        G = fbp.Graph(g, "RESIDUAL")
+        G.set_option(fbp.FBP_OPT_RESIDUAL_DEVICE, device_schedule)
+        status, it, res = G.run(400, 1e-7)
+        pa = G.marginals().astype(np.float64)
+        G.close()
+        assert status == fbp.FBP_OK, (g.name, it, res)
+        assert np.abs(pa - o.marginals(r_res["a2v"])).max() <= TOL_P, g.name
+        assert np.abs(pa - o.marginals(r_par["a2v"])).max() <= TOL_P, g.name
+        checked += 1
+    assert checked >= 5

@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
     unsigned long long ng = 0;
     unsigned target = 0;
     int it, status = 1, failed = 0;
+    const bool solo = gridDim.x == 1;  // one block: block barriers only
     const bool empty = A.n_halves == 0 ||
                        (A.half[0].n_levels == 0 && (A.n_halves < 2 || A.half[1].n_levels == 0));
     Pre<kPre> pre;
@@ -457,9 +458,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                     const float bm = block_max(rmax);
                     if (threadIdx.x == 0 && bm > 0.f) max_bits(A.res + (it - 1), __float_as_uint(bm));
                 }
+                // A one-block grid needs no grid barrier: __syncthreads orders
+                // the block's message stores before the next level's loads.
                 if (kCluster) {
                     cluster_arrive();
-                } else {
+                } else if (!solo) {
                     grid_arrive(A.bar);
                     target += gridDim.x;
                 }
@@ -467,6 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                 prefetch_b(pre, next, A, Pn, Ln + Pn.level_base);
                 if (kCluster) {
                     cluster_wait();
+                } else if (solo) {
+                    __syncthreads();
                 } else if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
                     failed = 1;
                     break;
@@ -482,6 +487,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
             if (kCluster) {
                 cluster_arrive();
                 cluster_wait();
+            } else if (solo) {
+                __syncthreads();
             } else {
                 grid_arrive(A.bar);
                 target += gridDim.x;

@@ -25,6 +25,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -95,12 +96,12 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="fbp_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.p = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}",
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -109,6 +110,13 @@ class Clocks:
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:  # noqa: BLE001
             self.p = None
+            if self.path:
+                try:
+                    self.f.close()
+                    os.remove(self.path)
+                except Exception:  # noqa: BLE001
+                    pass
+                self.path = None
         return self
 
     def __exit__(self, *exc):
@@ -121,11 +129,14 @@ class Clocks:
             self.f.close()
 
     def summary(self):
-        if self.p is None or not os.path.exists(self.path):
+        if self.p is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        os.remove(self.path)
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue

@@ -479,6 +479,61 @@ def hub_and_wide(n_hub: int = 3000, n_medium: int = 200, n_pool: int = 500, seed
                        f"hub{n_hub}_wide_s{seed}")
 
 
+def planted_alarms(g: FactorGraph, n_alarms: int, seed: int, fire: float = 0.6,
+                   base_true: float = 0.9) -> tuple[np.ndarray, np.ndarray]:
+    """Planted ground truth for an alarm-ranking run on a derivation graph
+    (tiny/bingo layout: tuples 0..n_tuples-1, NOISY_AND rule rows
+    [premises, d_r], OR rows [d_r..., conclusion]).  Base tuples (no OR
+    factor concludes them) are true with their prior, or with probability
+    base_true where they have none.  Each rule instance truly fires with
+    probability `fire` (the model assumes its own, higher p).  A derived tuple
+    is true iff some truly firing rule with all premises true derives it: the
+    least fixed point, reached by iterating from all derived tuples false, so
+    that a cycle supports nothing by itself.  Returns n_alarms distinct derived
+    tuples and their truth (int8)."""
+    rng = np.random.default_rng(seed)
+    n_t = int(g.meta["n_tuples"])
+    fp = np.asarray(g.factor_ptr, np.int64)
+    fv = np.asarray(g.factor_vars, np.int64)
+    ft = np.asarray(g.factor_type)
+    rules = np.flatnonzero(ft == NOISY_AND)
+    ors = np.flatnonzero(ft == OR)
+    out_of = lambda a: fv[fp[a + 1] - 1]                      # noqa: E731  output variable of factors a
+    concl = out_of(ors)
+    derived = np.zeros(n_t, bool)
+    derived[concl] = True
+    pr = np.asarray(g.prior_p1[:n_t], np.float64)
+    u = rng.random(n_t)
+    base_truth = ~derived & np.where(np.isnan(pr), u < base_true, u < np.nan_to_num(pr))
+    fires = rng.random(rules.size) < fire
+    # premise edges of every rule, and the rule each belongs to
+    r_len = fp[rules + 1] - fp[rules] - 1
+    r_prem = np.concatenate([fv[fp[a]:fp[a + 1] - 1] for a in rules]) if rules.size else np.zeros(0, np.int64)
+    r_of = np.repeat(np.arange(rules.size), r_len)
+    d_of_rule = out_of(rules)
+    # the OR factor (index into ors) that each derivation variable feeds
+    or_of_d = np.full(g.n_vars, -1, np.int64)
+    for k, a in enumerate(ors):
+        or_of_d[fv[fp[a]:fp[a + 1] - 1]] = k
+    truth = np.zeros(g.n_vars, bool)
+    truth[:n_t] = base_truth
+    while True:
+        bad = np.zeros(rules.size, np.int64)  # premises of each rule that are false
+        np.add.at(bad, r_of, ~truth[r_prem])
+        d_true = fires & (bad == 0)
+        c_true = np.zeros(ors.size, bool)
+        c_true[or_of_d[d_of_rule[d_true]]] = True
+        new = base_truth.copy()
+        new[concl[c_true]] = True
+        if np.array_equal(new, truth[:n_t]):
+            truth[d_of_rule] = d_true
+            break
+        truth[:n_t] = new
+    cand = np.flatnonzero(derived)
+    alarms = rng.choice(cand, size=min(n_alarms, cand.size), replace=False)
+    return alarms.astype(np.int64), truth[alarms].astype(np.int8)
+
+
 def random_terms(rng: np.random.Generator, b: int, max_terms: int = 6, free: float = 0.3,
                  floor: float = 0.0):
     """A random term list for a factor over b variables: 1..max_terms terms,

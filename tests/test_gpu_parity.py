@@ -316,10 +316,15 @@ def test_engine_grid_size_does_not_change_results(fbp, grid):
 
 def test_barrier_timeout_is_reported_and_context_survives(fbp):
     """Failure detection without a GPU fault: a spin limit of 0 makes every
-    device-side barrier wait expire at once; the run must return
-    FBP_ERR_TIMEOUT and the context must stay usable."""
-    g = gen.smartfl(n_layers=10, width=40, seed=63)
-    G = fbp.Graph(g, "TOPO_FB")
+    device-side barrier wait that has to wait at all expire at once; the run
+    must return FBP_ERR_TIMEOUT and the context must stay usable.  A wait is
+    made certain: under SEQFIX most levels hold one or two factors, and a
+    level whose factor has the 3,000-entry hub as a premise keeps one lane on
+    the hub's row for ~1e5 cycles while the other blocks of a 4-block grid
+    arrive and poll (on a balanced level every block can arrive before anyone
+    polls, and nothing waits)."""
+    g = gen.hub_and_wide(seed=71)
+    G = fbp.Graph(g, "SEQFIX")
     G.set_option(fbp.FBP_OPT_ENGINE_GRID, 4)
     G.set_option(fbp.FBP_OPT_SPIN_LIMIT, 0)
     with pytest.raises(fbp.FbpError) as ei:
@@ -331,7 +336,7 @@ def test_barrier_timeout_is_reported_and_context_survives(fbp):
     assert it == 3
     p = G.marginals()
     G.close()
-    ref = gpu_run(fbp, g, "TOPO_FB", 3, 0.0)
+    ref = gpu_run(fbp, g, "SEQFIX", 3, 0.0)
     assert np.array_equal(p.astype(np.float64), ref["p"])
 
 

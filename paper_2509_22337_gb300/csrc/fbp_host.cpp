@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <new>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -293,17 +294,21 @@ static int check_factor(int32_t nv, const int64_t *fptr, const int32_t *fvars, c
                                   : FBP_ERR_INVALID_ARG;
     }
     if (n > 64) {  // a wide factor: sort a copy; report the first repeat in row order
-        std::vector<int32_t> tmp(fvars + lo, fvars + lo + n);
-        std::sort(tmp.begin(), tmp.end());
-        if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) {
-            if (!report) return FBP_ERR_INVALID_ARG;
-            std::vector<int32_t> seen;
-            for (int64_t e = lo; e < lo + n; ++e) {
-                const auto it = std::lower_bound(seen.begin(), seen.end(), fvars[e]);
-                if (it != seen.end() && *it == fvars[e])
-                    return fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, fvars[e]);
-                seen.insert(it, fvars[e]);
+        try {  // (this may run on a worker thread: nothing may escape it)
+            std::vector<int32_t> tmp(fvars + lo, fvars + lo + n);
+            std::sort(tmp.begin(), tmp.end());
+            if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) {
+                if (!report) return FBP_ERR_INVALID_ARG;
+                std::vector<int32_t> seen;
+                for (int64_t e = lo; e < lo + n; ++e) {
+                    const auto it = std::lower_bound(seen.begin(), seen.end(), fvars[e]);
+                    if (it != seen.end() && *it == fvars[e])
+                        return fail(FBP_ERR_INVALID_ARG, "factor %d lists variable %d twice", a, fvars[e]);
+                    seen.insert(it, fvars[e]);
+                }
             }
+        } catch (const std::bad_alloc &) {
+            return report ? fail(FBP_ERR_OOM, "host memory exhausted checking factor %d", a) : FBP_ERR_OOM;
         }
     }
     const int t = ftype[a];

@@ -1,11 +1,13 @@
 """Autotuner for the launch shapes of the CUDA path.
 
 It times candidate launch shapes on the caller's own graph (or batch) and
-keeps the fastest.  Every knob it turns is result-invariant (the tests check
-bit-identical messages across them):
+keeps the fastest.  The engine's knobs leave every message bit-identical (the
+tests check it); the flooding split only regroups a long row's product, which
+can move its last bits (the tests check marginals within 1e-5):
 
 * static strategies (persistent level engine): grid mode with 1, 1/2 or 2
-  blocks per SM, one 16-block cluster, or one launch per level (the paper's
+  blocks per SM, a single block (block barriers between levels: for narrow
+  levels), one 16-block cluster, or one launch per level (the paper's
   execution);
 * flooding: how long a variable row may get before it is split over blocks
   (the threads-per-message split of long rows) and the split's chunk size.
@@ -84,7 +86,7 @@ def graph_candidates(strategy: str):
                 yield {F.FBP_OPT_FLOOD_HUB_MIN: hub, F.FBP_OPT_FLOOD_CHUNK: chunk}
         return
     yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: 0}
-    for grid in (sms // 2, sms, 2 * sms):
+    for grid in (1, sms // 2, sms, 2 * sms):
         yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: grid}
     yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 16, F.FBP_OPT_ENGINE_GRID: 0}
     yield {F.FBP_OPT_ENGINE: 0, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: 0}

@@ -216,7 +216,10 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  * FBP_OPT_FLOOD_HUB_MIN  flooding: variables with more incident factors than
  *                      this (8..256, default 256) are split over blocks.
  * FBP_OPT_FLOOD_CHUNK  flooding: entries of such a variable per block
- *                      (64..65536, default 1024).
+ *                      (a multiple of 256 in 256..65536, default 1024).
+ *                      Neither split option changes a result: a long row's
+ *                      product is grouped in 256-entry sub-chunks whichever
+ *                      kernel carries it, so messages are bit-identical.
  * FBP_OPT_RESIDUAL_DEVICE 1 (default): RESIDUAL builds each iteration's
  *                      classes and Algorithm 2 levels on the device and runs
  *                      the levels with the flooding kernels; 0: classes and

@@ -30,12 +30,15 @@ extern "C" {
 #define FBP_FIXED_SCRATCH_MAX_ITERS 16384
 #define FBP_FIXED_SCRATCH_BYTES (256 + 4 * FBP_FIXED_SCRATCH_MAX_ITERS)
 
-/* Run graph g from its current messages, exactly as fbp_run does for a
- * static strategy (SEQFIX, TOPO, TOPO_FB, CUSTOM_RANK; Sec. 4.2, Algorithm 2
- * levels, Eqs. 1-2 per message) with the persistent level engine in one
- * launch, stopping at the first iteration whose residual is below tol
- * (Sec. 4.1) or after max_iters iterations.  Same return values, outputs,
- * message state and fbp_get_stats figures as fbp_run on the same graph.
+/* Run graph g from its current messages as fbp_run does for a static
+ * strategy (SEQFIX, TOPO, TOPO_FB, CUSTOM_RANK), stopping at the first
+ * iteration whose residual is below tol or after max_iters iterations.  The
+ * paper has no counterpart of this call.  Same return values, outputs and
+ * message state as fbp_run on the same graph, bit for bit, and the same
+ * fbp_get_stats figures except kernel_launches: this call always runs the
+ * persistent level engine in one launch (kernel_launches = 1), also when
+ * FBP_OPT_ENGINE = 0 asks fbp_run for one launch per level, which computes
+ * the same messages.
  *
  * Memory: allocates no device memory (no cudaMalloc, no call of the graph's
  * allocator, no library routine that allocates).  The per-run scratch -- the

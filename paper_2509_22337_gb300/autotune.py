@@ -1,9 +1,10 @@
 """Autotuner for the launch shapes of the CUDA path.
 
 It times candidate launch shapes on the caller's own graph (or batch) and
-keeps the fastest.  The engine's knobs leave every message bit-identical (the
-tests check it); the flooding split only regroups a long row's product, which
-can move its last bits (the tests check marginals within 1e-5):
+keeps the fastest.  No knob changes the arithmetic: the engine's shapes and
+the flooding split (a long row's product is always grouped in 256-entry
+sub-chunks, whichever kernel carries it) leave every message bit-identical,
+which the tests check, so the timing-dependent pick never changes a result:
 
 * static strategies (persistent level engine): grid mode with 1, 1/2 or 2
   blocks per SM, a single block (block barriers between levels: for narrow

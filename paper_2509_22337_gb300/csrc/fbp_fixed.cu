@@ -69,6 +69,7 @@ int scratch_address(unsigned char **out)
 extern "C" int fbp_run_fixed_scratch(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out,
                                      double *residual_out)
 {
+    clear_error();  // fbp_last_error reports this call only
     if (!g) return fail(FBP_ERR_INVALID_ARG, "graph is NULL");
     if (max_iters < 0 || !(tol >= 0.0)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
     if (max_iters > FBP_FIXED_SCRATCH_MAX_ITERS)
@@ -99,6 +100,8 @@ extern "C" int fbp_run_fixed_scratch(fbp_graph *g, int32_t max_iters, double tol
     unsigned res_bits = 0;
     int status = FBP_NOT_CONVERGED;
     if (max_iters > 0) {
+        // always the persistent engine in one launch (the per-level launches
+        // of FBP_OPT_ENGINE=0 would compute the same messages)
         EngineArgs A = engine_args(g);
         A.guards = guards;
         A.bar = bar;

@@ -15,7 +15,19 @@
 //                             registers (multiply-only, as in the oracle)
 //   rows of degree <= 256     one warp per row
 //   longer rows (hubs)        chunks of kFloodHubChunk entries, one block each; a
-//                             pre-pass writes each chunk's partial product
+//                             pre-pass writes the partial product of each
+//                             256-entry sub-chunk
+// The row total of every row longer than 8 entries is grouped one way only,
+// whichever kernel carries the row: the row is cut into 256-entry sub-chunks;
+// lane l of a warp multiplies entries l, l+32, ..., l+224 of a sub-chunk in
+// that order and the 32 lane products are combined by an xor butterfly; the
+// sub-chunk products are then combined the same way (lane j takes sub-chunks
+// j, j+32, ... in order, then the butterfly).  A row of at most 256 entries is
+// one sub-chunk, so the warp-per-row path and the chunked path compute the
+// same bits, and the split thresholds (FBP_OPT_FLOOD_HUB_MIN, _CHUNK) only
+// move work between kernels.  Every multiply rounds the exact product once
+// (the mantissa/exponent form never goes subnormal), so only this grouping
+// decides the result.
 // Phase 2, the closed-form local-structure messages: one lane per message,
 // whole factors per warp, the factor's other messages by warp shuffle;
 // factors wider than a warp one thread per edge.
@@ -154,26 +166,43 @@ __device__ __forceinline__ float excl_msg(const XP &t, float phi, float rho_k)
 // ----------------------------------------------------------------------------
 // Phase 1
 // ----------------------------------------------------------------------------
+// Product of one 256-entry sub-chunk [b, end) of a row, by one warp, in the
+// canonical grouping (all lanes get it).  Entries past `end` multiply by 1,
+// which is exact.
+__device__ __forceinline__ XP sub_chunk_product(const DevGraph &g, const float *__restrict__ a2v, int b, int end,
+                                                int lane, int *e, float *r)
+{
+    const int ns = (end - b + 31) >> 5;  // slots in use (warp-uniform); the others would multiply by 1
+#pragma unroll
+    for (int u = 0; u < kFloodSub / 32; ++u)
+        e[u] = u < ns && b + lane + 32 * u < end ? __ldg(g.vedge + b + lane + 32 * u) : -1;
+#pragma unroll
+    for (int u = 0; u < kFloodSub / 32; ++u) r[u] = e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
+    XP t = xp_one();
+#pragma unroll
+    for (int u = 0; u < kFloodSub / 32; ++u)
+        if (u < ns) xmul(t, r[u]);
+    return warp_product(t);
+}
+
+// Partial products of the 256-entry sub-chunks of one chunk of a hub row; the
+// chunk's warps take its sub-chunks in turn.
 __global__ void __launch_bounds__(256) k_hub_partials(const DevGraph g, FloodPlanDev F,
                                                       const float *__restrict__ a2v)
 {
     if (*(volatile const int *)F.done) return;
     const int c = blockIdx.x;
-    const int4 ch = __ldg(F.hub + c);  // {var, begin, end, first chunk of the row}
+    const int4 ch = __ldg(F.hub + c);  // {var, begin, end, first sub-chunk of this chunk}
     if (var_frozen(F, ch.x)) return;   // block-uniform
-    XP t = xp_one();
-    for (int k0 = ch.y + threadIdx.x; k0 < ch.z; k0 += 4 * blockDim.x) {
-        int e[4];
-        float r[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = k0 + u * blockDim.x < ch.z ? __ldg(g.vedge + k0 + u * blockDim.x) : -1;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) r[u] = e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) xmul(t, r[u]);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nsub = (ch.z - ch.y + kFloodSub - 1) / kFloodSub;
+    for (int s = threadIdx.x >> 5; s < nsub; s += nw) {
+        int e[kFloodSub / 32];
+        float r[kFloodSub / 32];
+        const int b = ch.y + s * kFloodSub;
+        const XP t = sub_chunk_product(g, a2v, b, min(ch.z, b + kFloodSub), lane, e, r);
+        if (lane == 0) F.agg[ch.w + s] = t;
     }
-    t = block_product(t);
-    if (threadIdx.x == 0) F.agg[c] = t;
 }
 
 // Variables of degree 1 and 2 (most of a derivation graph: every rule's
@@ -244,44 +273,32 @@ __global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev
     }
     const int bm = b - F.nb_small;
     if (bm < F.nb_medium) {
-        // one warp per variable of degree in (kFloodSmallMax, kFloodMediumMax]
+        // one warp per variable of degree in (kFloodSmallMax, kFloodMediumMax]:
+        // the row is a single sub-chunk
         const int w = bm * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
         if (w >= F.n_medium) return;
         const int v = __ldg(F.medium + w);
         if (var_frozen(F, v)) return;
         const int lo = __ldg(g.vptr + v), hi = __ldg(g.vptr + v + 1);
-        // at most kFloodMediumMax / 32 = 8 entries per lane, all loads issued
-        // first; ns (uniform in the warp) skips the slots past the row
-        const int ns = (hi - lo + 31) >> 5;
-        int e[kFloodMediumMax / 32];
-        float r[kFloodMediumMax / 32];
-#pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u) {
-            e[u] = -1;
-            if (u < ns && lo + lane + 32 * u < hi) e[u] = __ldg(g.vedge + lo + lane + 32 * u);
-        }
-#pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u) r[u] = u < ns && e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
-        XP t = xp_one();
-#pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u)
-            if (u < ns) xmul(t, r[u]);  // a skipped slot would multiply by exactly 1
-        t = warp_product(t);
+        int e[kFloodSub / 32];
+        float r[kFloodSub / 32];
+        const XP t = sub_chunk_product(g, a2v, lo, hi, lane, e, r);
         const float phi = __ldg(g.phi + v);
 #pragma unroll
-        for (int u = 0; u < kFloodMediumMax / 32; ++u)
-            if (u < ns && e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
+        for (int u = 0; u < kFloodSub / 32; ++u)
+            if (e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
         return;
     }
-    // hub chunk: combine the row's chunk partials, then every entry of this chunk
+    // hub chunk: combine the row's sub-chunk partials (canonical grouping),
+    // then every entry of this chunk
     const int c = bm - F.nb_medium;
     const int4 ch = __ldg(F.hub + c);
     if (var_frozen(F, ch.x)) return;  // block-uniform
-    const int c0 = ch.w, nc = __ldg(F.hub_nchunks + c);
+    const int2 rs = __ldg(F.hub_row + c);  // {first sub-chunk of the row, sub-chunks of the row}
     __shared__ XP s_tot;
     if (threadIdx.x < 32) {
         XP t = xp_one();
-        for (int j = threadIdx.x; j < nc; j += 32) t = xcombine(t, F.agg[c0 + j]);
+        for (int j = threadIdx.x; j < rs.y; j += 32) t = xcombine(t, F.agg[rs.x + j]);
         t = warp_product(t);
         if (threadIdx.x == 0) s_tot = t;
     }

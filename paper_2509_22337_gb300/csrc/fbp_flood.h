@@ -16,6 +16,9 @@ struct XP {
 constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread each
 constexpr int kFloodMediumMax = 256;   // rows up to this degree: one warp each
 constexpr int kFloodHubChunk = 1024;   // longer rows: chunks of this many entries (one block)
+constexpr int kFloodSub = 256;         // the grouping unit of a long row's product (= kFloodMediumMax)
+static_assert(kFloodSub == kFloodMediumMax, "a warp-per-row row is exactly one sub-chunk");
+static_assert(kFloodHubChunk % kFloodSub == 0, "chunks hold whole sub-chunks");
 constexpr int kFloodChunk = 8;         // iterations per captured CUDA graph
 
 struct FloodPlanDev {
@@ -26,9 +29,9 @@ struct FloodPlanDev {
     int32_t n_medium = 0;
     const int32_t *medium = nullptr;   // [n_medium] variables of medium degree
     int32_t n_hub = 0;                 // hub chunks
-    const int4 *hub = nullptr;         // [n_hub] {variable, row begin, row end, first chunk of the row}
-    const int32_t *hub_nchunks = nullptr;  // [n_hub] chunks of the chunk's row
-    XP *agg = nullptr;                 // [n_hub] partial product of each chunk
+    const int4 *hub = nullptr;         // [n_hub] {variable, chunk begin, chunk end, first sub-chunk of the chunk}
+    const int2 *hub_row = nullptr;     // [n_hub] {first sub-chunk of the chunk's row, sub-chunks of the row}
+    XP *agg = nullptr;                 // [sub-chunks of all hub rows] partial product of each sub-chunk
     // phase 2: warps of whole consecutive factors; factors wider than a warp
     // edge by edge
     int32_t n_warps = 0;

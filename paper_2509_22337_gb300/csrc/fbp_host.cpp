@@ -29,6 +29,8 @@ namespace {
 thread_local std::string t_err;
 }  // namespace
 
+void fbp::clear_error() { t_err.clear(); }
+
 int fbp::fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -182,7 +184,7 @@ int build_flood_plan(fbp_graph *g)
         dfree(g, (void *)g->flood.small);
         dfree(g, (void *)g->flood.medium);
         dfree(g, (void *)g->flood.hub);
-        dfree(g, (void *)g->flood.hub_nchunks);
+        dfree(g, (void *)g->flood.hub_row);
         dfree(g, (void *)g->flood.agg);
         dfree(g, (void *)g->flood.warps);
         dfree(g, (void *)g->flood.wide);
@@ -192,7 +194,8 @@ int build_flood_plan(fbp_graph *g)
     FloodPlanDev F;
     std::vector<int32_t> small, medium;
     std::vector<int4> hub;
-    std::vector<int32_t> hub_n;
+    std::vector<int2> hub_row;
+    int32_t n_sub = 0;  // sub-chunks of all hub rows so far
     for (int32_t v = 0; v < h.nv; ++v) {
         const int32_t lo = h.vptr[v], hi = h.vptr[v + 1], d = hi - lo;
         if (d <= 2) continue;  // the lean kernel's rows
@@ -204,13 +207,13 @@ int build_flood_plan(fbp_graph *g)
             medium.push_back(v);
             continue;
         }
-        const int32_t ch = g->flood_chunk;
-        const int32_t c0 = (int32_t)hub.size();
-        const int32_t nc = (d + ch - 1) / ch;
+        const int32_t ch = g->flood_chunk;  // a multiple of kFloodSub
+        const int32_t nc = (d + ch - 1) / ch, ns = (d + kFloodSub - 1) / kFloodSub;
         for (int32_t c = 0; c < nc; ++c) {
-            hub.push_back(make_int4(v, lo + c * ch, std::min(hi, lo + (c + 1) * ch), c0));
-            hub_n.push_back(nc);
+            hub.push_back(make_int4(v, lo + c * ch, std::min(hi, lo + (c + 1) * ch), n_sub + c * (ch / kFloodSub)));
+            hub_row.push_back(make_int2(n_sub, ns));
         }
+        n_sub += ns;
     }
     // rows of one degree side by side: the per-row loops of a warp then run
     // to nearly the same length (each row is independent: same results)
@@ -225,19 +228,20 @@ int build_flood_plan(fbp_graph *g)
     F.n_medium = (int32_t)medium.size();
     F.nb_medium = (F.n_medium + 7) / 8;
     F.n_hub = (int32_t)hub.size();
-    int32_t *d_small = nullptr, *d_medium = nullptr, *d_hub_n = nullptr;
+    int32_t *d_small = nullptr, *d_medium = nullptr;
     int4 *d_hub = nullptr;
+    int2 *d_hub_row = nullptr;
     XP *d_agg = nullptr;
     int rc = upload(g, &d_small, small.data(), small.size());
     if (!rc) rc = upload(g, &d_medium, medium.data(), medium.size());
     if (!rc) rc = upload(g, &d_hub, hub.data(), hub.size());
-    if (!rc) rc = upload(g, &d_hub_n, hub_n.data(), hub_n.size());
-    if (!rc) rc = dalloc_n(g, &d_agg, std::max<size_t>(hub.size(), 1));
+    if (!rc) rc = upload(g, &d_hub_row, hub_row.data(), hub_row.size());
+    if (!rc) rc = dalloc_n(g, &d_agg, std::max<size_t>(n_sub, 1));
     if (rc) return rc;
     F.small = d_small;
     F.medium = d_medium;
     F.hub = d_hub;
-    F.hub_nchunks = d_hub_n;
+    F.hub_row = d_hub_row;
     F.agg = d_agg;
     // phase 2: consecutive whole factors packed into warps of at most 32 edges;
     // a factor wider than a warp goes edge by edge to the wide list
@@ -1182,7 +1186,8 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         g->flood_ready = false;  // rebuilt at the next flooding run
         return FBP_OK;
     case FBP_OPT_FLOOD_CHUNK:
-        if (value < 64 || value > (1 << 16)) return fail(FBP_ERR_INVALID_ARG, "chunk must be in [64, 65536]");
+        if (value < kFloodSub || value > (1 << 16) || value % kFloodSub != 0)
+            return fail(FBP_ERR_INVALID_ARG, "chunk must be a multiple of %d in [%d, 65536]", kFloodSub, kFloodSub);
         g->flood_chunk = (int)value;
         g->flood_ready = false;
         return FBP_OK;

@@ -64,6 +64,8 @@ struct HostCSR {
 
 // Sets the thread-local error message; returns code.
 int fail(int code, const char *fmt, ...);
+// Clear the thread's last error message (entry points call it first).
+void clear_error();
 
 void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars,
                     const uint8_t *ftype, const float *fparam, HostCSR &h);

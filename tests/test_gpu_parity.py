@@ -127,16 +127,16 @@ def test_small_graphs_all_strategies(fbp, strategy):
     assert checked >= 2
 
 
-@pytest.mark.parametrize("strategy,split", [("PARALL", None), ("PARALL", (9, 64)), ("SEQFIX", None),
+@pytest.mark.parametrize("strategy,split", [("PARALL", None), ("PARALL", (9, 256)), ("SEQFIX", None),
                                             ("TOPO_FB", None)])
 def test_hub_rows_and_wide_factors_vs_oracle(fbp, strategy, split):
-    """A 3,000-entry hub row (three full 1,024-entry chunks and a ragged tail),
+    """A 3,000-entry hub row (two full 1,024-entry chunks and a ragged one),
     a 200-entry row, and four factors wider than a warp (40, 35, 34 and 41
     variables), element by element against the oracle: flooding (hub chunks,
     warp rows, the wide-factor kernel) and the engine (long rows, the per-edge
     path of wide factors).  split = (hub_min, chunk) reconfigures the flooding
-    work split so that rows above 9 entries run in 64-entry chunks: the hub in
-    47 chunks with a 56-entry tail, the 200-entry row in 4 with an 8-entry tail."""
+    work split so that rows above 9 entries run in 256-entry chunks: the hub in
+    12 chunks with a 184-entry tail, the 200-entry row as one ragged chunk."""
     for seed in (71, 72):
         g = gen.hub_and_wide(seed=seed)
         b = oracle_run(g, strategy, 12, 0.0)
@@ -156,6 +156,26 @@ def test_hub_rows_and_wide_factors_vs_oracle(fbp, strategy, split):
         assert abs(p[0] - b["p"][0]) <= TOL_P
         print(f"{g.name} {strategy} {split}: max |dp| {err:.2e}, "
               f"max |d m1| {np.abs(m[:, 1] - b['a2v'][:, 1]).max():.2e}")
+
+
+@pytest.mark.parametrize("graph", [lambda: gen.hub_and_wide(seed=73), lambda: gen.bingo(n_tuples=30000, seed=74)])
+def test_flood_split_is_arithmetic_invariant(fbp, graph):
+    """The flooding split only moves rows between kernels: every (hub_min,
+    chunk) setting the tuner may pick computes the same messages bit for bit
+    (a row's product is always grouped in 256-entry sub-chunks)."""
+    g = graph()
+    ref = None
+    for hub_min, chunk in [(256, 1024), (9, 256), (64, 512), (128, 2048), (9, 65536), (200, 768)]:
+        G = fbp.Graph(g, "PARALL")
+        G.set_option(fbp.FBP_OPT_FLOOD_HUB_MIN, hub_min)
+        G.set_option(fbp.FBP_OPT_FLOOD_CHUNK, chunk)
+        G.run(15, 0.0)
+        m, p = G.messages(), G.marginals()
+        G.close()
+        if ref is None:
+            ref = (m, p)
+            continue
+        assert np.array_equal(m, ref[0]) and np.array_equal(p, ref[1]), (hub_min, chunk)
 
 
 def test_levels_from_device_graph_match_oracle(fbp):

@@ -742,6 +742,18 @@ static int64_t residual_active(const og_graph *g, const double *dres, double tol
     return n;
 }
 
+/* Exposed for the tests: the residual strategy's class of every edge (rank,
+ * -1 = skipped) and its active edges, from given previous-iteration per-edge
+ * |delta m1| values.  Returns the number of active edges. */
+int64_t orc_residual_classes(const og_graph *g, const double *dres, double tol, int64_t *rank,
+                             int64_t *edges)
+{
+    double *vres = (double *)malloc(sizeof(double) * (g->nv + 1));
+    int64_t n = residual_active(g, dres, tol, rank, edges, vres);
+    free(vres);
+    return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Full run.  a2v holds 2*E doubles: (m0, m1) per edge; if init is zero it   */
 /* is set to the uniform message first (reading: initial messages).          */

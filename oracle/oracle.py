@@ -86,6 +86,8 @@ def lib():
             L.orc_v2a_row.restype = C.c_int
             L.orc_update_edges.argtypes = [C.c_void_p, _f64, C.c_int64, _i64, _f64]
             L.orc_update_edges.restype = C.c_int
+            L.orc_residual_classes.argtypes = [C.c_void_p, _f64, C.c_double, _i64, _i64]
+            L.orc_residual_classes.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -215,3 +217,11 @@ class Oracle:
         lib().orc_update_edges(self._h, np.ascontiguousarray(a2v, np.float64).reshape(-1),
                                int(edges.shape[0]), edges, out)
         return out[: 2 * edges.shape[0]].reshape(-1, 2)
+
+    def residual_classes(self, dres: np.ndarray, tol: float):
+        """The residual strategy's classes from previous-iteration per-edge
+        |delta m1| values: (rank per edge, -1 = skipped; active edges)."""
+        rank = np.zeros(self.n_edges + 1, dtype=np.int64)
+        edges = np.zeros(self.n_edges + 1, dtype=np.int64)
+        n = lib().orc_residual_classes(self._h, np.ascontiguousarray(dres, np.float64), float(tol), rank, edges)
+        return rank[: self.n_edges].copy(), edges[:n].copy()

@@ -226,7 +226,7 @@ def _tree_cases():
     return cases
 
 
-@pytest.mark.parametrize("strategy", ["PARALL", "SEQFIX", "TOPO", "RESIDUAL"])
+@pytest.mark.parametrize("strategy", ["PARALL", "SEQFIX", "TOPO", "TOPO_FB", "RESIDUAL"])
 def test_bp_exact_on_trees(strategy):
     checked = 0
     for g in _tree_cases():
@@ -362,6 +362,115 @@ def test_topo_rejects_cycles():
     o = O.Oracle(g)
     with pytest.raises(ValueError):
         o.ranks("TOPO")
+
+
+def _chain(n, seed):
+    """x0 -> x1 -> ... -> x{n-1}: factor i has premise x{i-1} and output x{i};
+    every variable has a prior, the last one is observed."""
+    rng = np.random.default_rng(seed)
+    types = rng.choice([gen.NOT, gen.EQ, gen.AND, gen.OR, gen.NOISY_IMPLY, gen.NOISY_AND], n - 1)
+    fv = np.array([[i - 1, i] for i in range(1, n)], np.int32).reshape(-1)
+    prior = rng.uniform(0.1, 0.9, n).astype(np.float32)
+    ev = np.full(n, -1, np.int8)
+    ev[-1] = 1
+    param = np.where((types == gen.NOISY_IMPLY) | (types == gen.NOISY_AND), rng.uniform(0.6, 0.95, n - 1), 0)
+    return gen.FactorGraph(n, np.arange(0, 2 * n - 1, 2, dtype=np.int64), fv, types.astype(np.uint8),
+                           param.astype(np.float32), prior, ev, f"chain{n}")
+
+
+def test_topo_fb_chain_exact_after_one_sweep():
+    """Reading 8 (Table 1's topological order, swept forward then backward):
+    on a chain the forward half carries every message towards the outputs
+    exactly and the backward half every message towards the premises, so one
+    TOPO_FB iteration gives the exact marginals (Sec. 3.2: BP is exact on
+    trees).  Two forward halves (or two backward halves) do not."""
+    for seed in range(6):
+        g = _chain(9, seed)
+        exact, Z = R.brute_force_marginals(g)
+        assert Z > 0
+        o = O.Oracle(g)
+        r = o.run("TOPO_FB", 1, 0.0)
+        np.testing.assert_allclose(o.marginals(r["a2v"]), exact, atol=1e-12, err_msg=g.name)
+        assert r["updates"] == 2 * g.n_edges  # one sweep = both halves, E writes each
+        twice_forward = o.marginals(o.run("TOPO", 2, 0.0)["a2v"])
+        assert np.abs(twice_forward - exact).max() > 1e-6
+
+
+def test_topo_fb_iteration_is_forward_levels_then_backward_levels():
+    """Reading 8: one TOPO_FB iteration is the TOPO level list (ranks = output
+    depth, pinned by test_topo_rank_is_layer_depth) followed by the level list
+    of the reversed ranks (max - rank), the second from the messages the first
+    left; the iteration's residual (reading 6) is the largest change of either
+    half's writes.  The reversed ranks are run as a custom preorder (Table 1)."""
+    first_bigger = second_bigger = 0
+    for seed in range(4):
+        g = gen.smartfl(n_layers=8, width=12, seed=90 + seed, planted=True)
+        o = O.Oracle(g)
+        fwd = o.ranks("TOPO")
+        bwd = fwd.max() - fwd
+        m0 = None
+        for k in range(4):  # start states: uniform, then after k PARALL iterations
+            if k:
+                m0 = o.run("PARALL", k, 0.0)["a2v"]
+            r = o.run("TOPO_FB", 1, 0.0, a2v=m0)
+            rf = o.run("TOPO", 1, 0.0, a2v=m0)
+            rb = o.run("CUSTOM", 1, 0.0, custom=bwd, a2v=rf["a2v"])
+            assert np.array_equal(r["a2v"], rb["a2v"]), (seed, k)
+            assert r["residual"] == max(rf["residual"], rb["residual"]), (seed, k)
+            first_bigger += rf["residual"] > rb["residual"]
+            second_bigger += rb["residual"] > rf["residual"]
+    # both halves set the residual somewhere, so a residual of one half only fails
+    assert first_bigger and second_bigger
+
+
+def test_topo_fb_stops_on_the_pair_residual():
+    """The stopping test (reading 6) applies once per forward + backward pair:
+    the iteration count is the first pair whose residual is below tol, and the
+    recorded history is one residual per pair."""
+    g = gen.smartfl(n_layers=8, width=12, seed=95, planted=True)
+    o = O.Oracle(g)
+    full = o.run("TOPO_FB", 40, 0.0, history=True)
+    h = full["res_hist"]
+    assert h.shape[0] == 40 and h[-1] < h[0]
+    tol = float(h[5]) * 1.000001  # pair 6 is the first below tol only if h[0..4] are above it
+    want = next(i for i in range(40) if h[i] < tol) + 1
+    r = o.run("TOPO_FB", 40, tol)
+    assert r["converged"] and r["iters"] == want
+    assert r["updates"] == 2 * g.n_edges * want
+
+
+def test_residual_classes_by_hand():
+    """Reading 9, the residual strategy's classes, on a hand-made graph whose
+    previous-iteration changes are set by hand: rho_a is the largest change
+    written into ANY of a's variables (by any factor), bucketed >= 1e-2 (0),
+    [1e-4, 1e-2) (1), [tol, 1e-4) (2), below tol skipped."""
+    tol = 1e-6
+    rows = [[0, 1], [2, 3], [4, 5], [6, 7], [8, 9], [10, 11], [1, 16], [12, 13], [13, 14], [14, 15]]
+    ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    fv = np.array([v for r in rows for v in r], np.int32)
+    n_a = len(rows)
+    g = gen.FactorGraph(17, ptr, fv, np.full(n_a, gen.EQ, np.uint8), np.zeros(n_a, np.float32),
+                        np.full(17, np.nan, np.float32), np.full(17, -1, np.int8), "hand")
+    dres = np.zeros(g.n_edges + 1)
+
+    def edge(a, v):
+        return int(ptr[a] + rows[a].index(v))
+    dres[edge(0, 0)] = 0.5      # a0: 0.5 -> class 0
+    dres[edge(0, 1)] = 2e-3     # into v1: a6 sees it through v1 only
+    dres[edge(1, 3)] = 1e-2     # a1: exactly 1e-2 -> class 0
+    dres[edge(2, 4)] = 5e-3     # a2: class 1
+    dres[edge(3, 7)] = 1e-4     # a3: exactly 1e-4 -> class 1
+    dres[edge(4, 8)] = 5e-5     # a4: class 2
+    dres[edge(5, 10)] = 1e-6    # a5: exactly tol -> class 2
+    dres[edge(7, 12)] = 9.9e-7  # a7: below tol -> skipped
+    dres[edge(8, 14)] = 3e-5    # a8: class 2 from its own write into v14 ...
+    dres[edge(9, 15)] = 0.2     # a9: ... while a9 (also at v14) is class 0 from v15
+    # a6 ([1, 16]) writes nothing itself: class 1 from a0's write into v1
+    want_cls = [0, 0, 1, 1, 2, 2, 1, -1, 2, 0]
+    o = O.Oracle(g)
+    rank, active = o.residual_classes(dres, tol)
+    assert rank.tolist() == [c for a, c in enumerate(want_cls) for _ in rows[a]]
+    assert active.tolist() == [e for a, c in enumerate(want_cls) if c >= 0 for e in range(ptr[a], ptr[a + 1])]
 
 
 def test_residual_reaches_parall_fixed_point():

@@ -135,7 +135,7 @@ int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_a
         if ((rc = upload(g, &P.vgraph, var_graph.data(), var_graph.size())) ||
             (rc = upload(g, &P.fgraph, fac_graph.data(), fac_graph.size())) || (rc = build_flood_plan(g)))
             return rc;
-        if (!g->v2a && (rc = dalloc_n(g, &g->v2a, (size_t)g->h.ne))) return rc;
+        if (!g->a2v_vm && (rc = dalloc_n(g, &g->a2v_vm, (size_t)g->h.ne))) return rc;
         return FBP_OK;
     }
     // static parts: each member's own levels, merged by level index
@@ -238,6 +238,8 @@ int run_flood(fbp_batch *b, Part &P)
     if (P.max_iters == 0) return FBP_OK;
     cudaGraphExec_t exec = nullptr;
     if ((rc = flood_exec_for(g, F, 0.f, kFloodChunk, &exec))) return rc;
+    flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, g->stream);  // after the reset of part_reset_state
+    b->stats.kernel_launches += g->h.ne > 0;
     g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
     g->h_out[3] = P.max_iters;
     e = cudaMemcpyAsync(g->d_out, g->h_out, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, g->stream);

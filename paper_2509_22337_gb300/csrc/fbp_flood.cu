@@ -2,35 +2,49 @@
 // distribution (BINGO-shaped derivation graphs have hub variables with 1e5
 // incident factors next to millions of degree-2 variables).
 //
-// Phase 1, Eq. (1): mu_{v->a} = phi_v * prod_{b != a} mu_{b->v}.  Instead of
-// prefix/suffix products (scans), each variable row is reduced once to its
-// total product and every entry's message is total / own factor.  This is
+// Phase 1, Eq. (1) in belief form: every variable's belief
+//   b_v = phi_v * prod_{a in N(v)} mu_{a->v}
+// is reduced once, from a variable-major copy of the a->v messages that each
+// row reads contiguously, and stored as a compact ratio record (8 bytes);
+// mu_{v->a} = b_v / mu_{a->v} is then formed where phase 2 needs it.  This is
 // exact in the algebra of the messages as long as (i) exact zeros (hard
 // messages) are counted rather than multiplied in, and (ii) the product never
-// underflows: each of the two entries is kept as a mantissa in [1/2, 1) and an
-// integer exponent.  Rounding is one multiply per factor (tree-shaped across
-// lanes and blocks for long rows) and one divide per entry.
-//   rows of degree 1 or 2     one thread per row (lean kernel)
-//   rows of degree 3..8       one thread per row; prefix/suffix products in
-//                             registers (multiply-only, as in the oracle)
-//   rows of degree <= 256     one warp per row
-//   longer rows (hubs)        chunks of kFloodHubChunk entries, one block each; a
-//                             pre-pass writes the partial product of each
-//                             256-entry sub-chunk
-// The row total of every row longer than 8 entries is grouped one way only,
-// whichever kernel carries the row: the row is cut into 256-entry sub-chunks;
-// lane l of a warp multiplies entries l, l+32, ..., l+224 of a sub-chunk in
-// that order and the 32 lane products are combined by an xor butterfly; the
-// sub-chunk products are then combined the same way (lane j takes sub-chunks
-// j, j+32, ... in order, then the butterfly).  A row of at most 256 entries is
-// one sub-chunk, so the warp-per-row path and the chunked path compute the
-// same bits, and the split thresholds (FBP_OPT_FLOOD_HUB_MIN, _CHUNK) only
-// move work between kernels.  Every multiply rounds the exact product once
-// (the mantissa/exponent form never goes subnormal), so only this grouping
-// decides the result.
-// Phase 2, the closed-form local-structure messages: one lane per message,
-// whole factors per warp, the factor's other messages by warp shuffle;
-// factors wider than a warp one thread per edge.
+// underflows: each of the two entries is kept as a mantissa and an integer
+// exponent while the row is reduced.
+//   rows of degree <= 8       one thread per row, entries in row order
+//   longer rows               one thread per 32-entry sub-chunk; a row of
+//                             2..8 sub-chunks (at most FBP_OPT_FLOOD_HUB_MIN
+//                             entries) combined by one thread, a longer one
+//                             by one warp
+// The product of every row longer than 8 entries is grouped one way only,
+// whichever kernel carries the row: the row is cut into 32-entry sub-chunks,
+// each multiplied in order; sub-chunk s goes to slot s mod 32 (a slot
+// multiplies its sub-chunks in order), and the 32 slots are combined by an
+// xor butterfly (slot j with slot j^16, then j^8, j^4, j^2, j^1).  A row of at
+// most 256 entries fills slots 0..7 only, and the one-thread combine
+// evaluates exactly that butterfly, so the thread and the warp combines
+// compute the same bits and the split options (FBP_OPT_FLOOD_HUB_MIN,
+// _CHUNK) only move work between kernels.  phi_v is multiplied in last.  Every multiply
+// rounds the exact product once (the mantissa/exponent form never goes
+// subnormal), so only this grouping decides the result.
+//
+// Phase 2, the closed-form local-structure messages (Eq. 4).  Every v->a
+// message is formed from its variable's belief and the edge's current a->v
+// message; the new a->v message is written in place (factor-major) and into
+// the variable-major copy.  Typed factors of at most 4 variables (most of a
+// derivation graph): one thread per factor over every factor id, prefix and
+// suffix products in registers; typed factors of 5..8 variables: the same
+// from a list of their ids.  Generic factors and typed factors of 9..32
+// variables: one lane per message, whole consecutive factors per warp, the
+// factor's other messages by warp shuffle.  Factors wider than a warp: one
+// thread per edge.
+//
+// Memory traffic per iteration: phase 1 streams the variable-major copy,
+// the row offsets and phi and writes one record per variable; phase 2
+// streams the factor-major variables, the variable-major slots and the
+// messages (read and write), gathers one belief record per edge (an array of
+// 8 bytes per variable, small enough to stay in L2) and scatters one message
+// per edge into the variable-major copy.
 #include "fbp_msg.cuh"
 #include "fbp_flood.h"
 
@@ -46,46 +60,78 @@ __device__ __forceinline__ bool var_frozen(const FloodPlanDev &F, int v)
     return F.batch.n_graphs > 0 && __ldcg(F.batch.done + __ldg(F.vgraph + v)) != 0;
 }
 
-// Multiply entry (m, e, z) by x in [0, 1]: exact zeros are counted; the
-// mantissa is renormalised into [1/2, 1) only when the product falls below
-// 2^-60, so the common case is one multiply and one compare.
+// x in (0, 1] as mantissa * 2^exponent with the mantissa in [1, 2): integer
+// operations for a normal x, frexpf (out of line) for a subnormal one.
+__device__ __noinline__ float2 split_subnormal(float x)
+{
+    int ex;
+    const float m = frexpf(x, &ex);  // [1/2, 1)
+    return make_float2(2.f * m, __int_as_float(ex - 1));
+}
+
+__device__ __forceinline__ float split(float x, int &ex)
+{
+    const int bits = __float_as_int(x);
+    ex = (bits >> 23) - 127;
+    if (ex == -127) {
+        const float2 me = split_subnormal(x);
+        ex = __float_as_int(me.y);
+        return me.x;
+    }
+    return __int_as_float((bits & 0x007fffff) | 0x3f800000);
+}
+
+// Multiply entry (m, e, z), mantissa m in [1, 2), by x in [0, 1]: exact zeros
+// are counted; the product of the mantissas rounds the exact product once and
+// is halved (exactly) back into [1, 2), so nothing ever goes subnormal.
 __device__ __forceinline__ void xmul1(float &m, int &e, int &z, float x)
 {
     if (x == 0.f) {
         ++z;
         return;
     }
-    const float p = m * x;
-    if (p < 0x1p-60f) {
-        int em, ex, pe;
-        const float mm = frexpf(m, &em), mx = frexpf(x, &ex);
-        m = frexpf(mm * mx, &pe);
-        e += em + ex + pe;
-        return;
+    int ex;
+    const float mx = split(x, ex);
+    m *= mx;
+    e += ex;
+    if (m >= 2.f) {
+        m *= 0.5f;
+        e += 1;
     }
-    m = p;
 }
 
+// Multiply by a rho-encoded message: its larger entry is 1, so only the
+// other entry multiplies.
 __device__ __forceinline__ void xmul(XP &t, float rho)
 {
-    const P2 x = dec(rho);
-    xmul1(t.m0, t.e0, t.z0, x.m0);
-    xmul1(t.m1, t.e1, t.z1, x.m1);
+    const bool neg = signbit(rho);  // (1, |rho|), else (|rho|, 1)
+    float m = neg ? t.m1 : t.m0;
+    int e = neg ? t.e1 : t.e0, z = neg ? t.z1 : t.z0;
+    xmul1(m, e, z, fabsf(rho));
+    if (neg) {
+        t.m1 = m; t.e1 = e; t.z1 = z;
+    } else {
+        t.m0 = m; t.e0 = e; t.z0 = z;
+    }
 }
 
+// Product of two partial products (mantissas in [1, 2): the product rounds
+// once and is halved back into [1, 2) exactly).
 __device__ __forceinline__ XP xcombine(const XP &a, const XP &b)
 {
     XP r;
-    float p0 = a.m0 * b.m0, p1 = a.m1 * b.m1;
+    r.m0 = a.m0 * b.m0;
+    r.m1 = a.m1 * b.m1;
     r.e0 = a.e0 + b.e0;
     r.e1 = a.e1 + b.e1;
-    int k0, k1;
-    p0 = frexpf(p0, &k0);
-    p1 = frexpf(p1, &k1);
-    r.m0 = p0;
-    r.m1 = p1;
-    r.e0 += k0;
-    r.e1 += k1;
+    if (r.m0 >= 2.f) {
+        r.m0 *= 0.5f;
+        r.e0 += 1;
+    }
+    if (r.m1 >= 2.f) {
+        r.m1 *= 0.5f;
+        r.e1 += 1;
+    }
     r.z0 = a.z0 + b.z0;
     r.z1 = a.z1 + b.z1;
     return r;
@@ -103,6 +149,8 @@ __device__ __forceinline__ XP xshfl_xor(const XP &t, int o)
     return r;
 }
 
+// Butterfly product over the warp; multiplication commutes, so every lane
+// ends with the same bits.
 __device__ __forceinline__ XP warp_product(XP t)
 {
 #pragma unroll
@@ -110,211 +158,177 @@ __device__ __forceinline__ XP warp_product(XP t)
     return t;
 }
 
-// Block-wide product (all threads get the result).  blockDim.x <= 1024.
-__device__ __forceinline__ XP block_product(XP t)
+// Belief record: the belief's two entries as the ratio b0/b1.
+//   x = bits of q = m0/m1 of the mantissas (both lie in [1, 2), so q lies in
+//       (1/2, 2)),
+//   y = (e0 - e1) * 16 + min(z0, 2) * 4 + min(z1, 2): the exponent
+//       difference (clamped to +-2^26; anything beyond +-400 saturates the
+//       final message anyway) and the zero counts (two tell "zero even
+//       without the own message" as well as any larger count).
+__device__ __forceinline__ uint2 belief_pack(const XP &t)
 {
-    __shared__ XP s_x[32];
-    t = warp_product(t);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if (lane == 0) s_x[w] = t;
-    __syncthreads();
-    XP u = lane < nw ? s_x[lane] : xp_one();
-    u = warp_product(u);
-    return u;
+    const float q = t.m0 * rcp_approx(t.m1);  // within a few ulp of the quotient
+    const int de = max(-(1 << 26), min(1 << 26, t.e0 - t.e1));
+    return make_uint2(__float_as_uint(q), (unsigned)(de * 16 + min(t.z0, 2) * 4 + min(t.z1, 2)));
 }
 
-// frexp of an entry that is nonzero, or of 1 for an entry counted as zero.
-__device__ __forceinline__ float fx(float x, int &e)
+// r * 2^E by two exact power-of-two factors (each exponent clamped to the
+// normal range), so a result in the normal range rounds once; far outside it
+// the result saturates to 0 or infinity, as the exact one would in FP32.
+__device__ __forceinline__ float scale2(float r, int E)
 {
-    return frexpf(x == 0.f ? 1.f : x, &e);
+    E = max(-300, min(300, E));
+    const int e1 = E / 2, e2 = E - e1;
+    r *= __int_as_float((127 + max(-126, min(127, e1))) << 23);
+    return r * __int_as_float((127 + max(-126, min(127, e2))) << 23);
 }
 
-// v->a message of an entry with factor rho_k, from the row total t and phi:
-// phi * t / x_k, encoded; zero mass -> uniform.  The ratio of the two entries
-// is (t0 f0 x1) / (t1 f1 x0), formed from mantissas in [1/2, 1) and an exponent
-// difference, so nothing underflows before the final encoding.
-__device__ __forceinline__ float excl_msg(const XP &t, float phi, float rho_k)
+// v->a message of an edge whose variable has belief record b and whose own
+// incoming a->v message is rho (Eq. 1: phi times every other incoming
+// message, i.e. the belief without the own message), encoded; zero mass
+// becomes the uniform message.  With the own message's entries x0, x1 the
+// result's ratio is (b0/b1) / (x0/x1); a zero own entry was counted in the
+// belief rather than multiplied, so it divides out as 1.  Mantissas and
+// exponents are split with integer operations; quotients go through the
+// approximate reciprocal (a few ulp).
+__device__ __forceinline__ float v2a_from_belief(uint2 b, float rho)
 {
-    const P2 f = dec(phi), x = dec(rho_k);
-    const int z0 = t.z0 - (x.m0 == 0.f) + (f.m0 == 0.f);
-    const int z1 = t.z1 - (x.m1 == 0.f) + (f.m1 == 0.f);
+    const int w = (int)b.y;
+    const float a = fabsf(rho);
+    const bool neg = signbit(rho);  // own message (1, a), else (a, 1)
+    const int z0 = ((w >> 2) & 3) - (!neg && a == 0.f);
+    const int z1 = (w & 3) - (neg && a == 0.f);
     if (z0 > 0 && z1 > 0) return 1.f;  // zero mass: uniform
     if (z0 > 0) return 0.f;            // hard (0, 1)
     if (z1 > 0) return -0.f;           // hard (1, 0)
-    const float f0 = f.m0 == 0.f ? 1.f : f.m0, f1 = f.m1 == 0.f ? 1.f : f.m1;
-    const float x0 = x.m0 == 0.f ? 1.f : x.m0, x1 = x.m1 == 0.f ? 1.f : x.m1;
-    float n0, n1;
-    int de;
-    if (fminf(fminf(f0, f1), fminf(x0, x1)) >= 0x1p-30f) {
-        // t.m >= 2^-60 and the rest >= 2^-30: both products stay normal
-        n0 = t.m0 * f0 * x1;
-        n1 = t.m1 * f1 * x0;
-        de = t.e0 - t.e1;
-    } else {
-        int ef0, ef1, ex0, ex1;
-        n0 = t.m0 * fx(f0, ef0) * fx(x1, ex1);
-        n1 = t.m1 * fx(f1, ef1) * fx(x0, ex0);
-        de = (t.e0 + ef0 + ex1) - (t.e1 + ef1 + ex0);
+    float r = __uint_as_float(b.x);    // in (1/2, 2)
+    int E = w >> 4;
+    if (a != 0.f) {
+        int ea;
+        const float ma = split(a, ea);  // [1, 2)
+        r = neg ? r * ma : r * rcp_approx(ma);
+        E += neg ? ea : -ea;
     }
-    de = max(-400, min(400, de));
-    const float r = ldexpf(__fdiv_rn(n0, n1), de);
+    r = scale2(r, E);
     if (r <= 1.f) return r;            // m1 is the larger entry
-    return -__frcp_rn(r);              // m0 is the larger entry
+    return -rcp_approx(r);             // m0 is the larger entry
+}
+
+// Product of entries x[b, end) in order (at most one sub-chunk), one thread;
+// every load is issued first.  Entries past the warp's longest run are
+// skipped by a uniform branch (a padded entry would multiply by exactly 1).
+__device__ __forceinline__ XP seq_product(const float *__restrict__ x, int b, int end)
+{
+    float r[kFloodSub];
+#pragma unroll
+    for (int u = 0; u < kFloodSub; ++u) r[u] = b + u < end ? __ldg(x + b + u) : 1.f;
+    const int nw = __reduce_max_sync(__activemask(), end - b);
+    XP t = xp_one();
+#pragma unroll
+    for (int u = 0; u < kFloodSub; ++u)
+        if (u < nw) xmul(t, r[u]);
+    return t;
 }
 
 // ----------------------------------------------------------------------------
 // Phase 1
 // ----------------------------------------------------------------------------
-// Product of one 256-entry sub-chunk [b, end) of a row, by one warp, in the
-// canonical grouping (all lanes get it).  Entries past `end` multiply by 1,
-// which is exact.
-__device__ __forceinline__ XP sub_chunk_product(const DevGraph &g, const float *__restrict__ a2v, int b, int end,
-                                                int lane, int *e, float *r)
+__global__ void k_sync_vm(const DevGraph g, const float *__restrict__ a2v, float *__restrict__ a2v_vm)
 {
-    const int ns = (end - b + 31) >> 5;  // slots in use (warp-uniform); the others would multiply by 1
-#pragma unroll
-    for (int u = 0; u < kFloodSub / 32; ++u)
-        e[u] = u < ns && b + lane + 32 * u < end ? __ldg(g.vedge + b + lane + 32 * u) : -1;
-#pragma unroll
-    for (int u = 0; u < kFloodSub / 32; ++u) r[u] = e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
-    XP t = xp_one();
-#pragma unroll
-    for (int u = 0; u < kFloodSub / 32; ++u)
-        if (u < ns) xmul(t, r[u]);
-    return warp_product(t);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < g.ne) a2v_vm[k] = a2v[__ldg(g.vedge + k)];
 }
 
-// Partial products of the 256-entry sub-chunks of one chunk of a hub row; the
-// chunk's warps take its sub-chunks in turn.
-__global__ void __launch_bounds__(256) k_hub_partials(const DevGraph g, FloodPlanDev F,
-                                                      const float *__restrict__ a2v)
+// Products of the 32-entry sub-chunks of the rows longer than 8 entries, one
+// thread per sub-chunk; a row of one sub-chunk gets its belief here.
+__global__ void __launch_bounds__(256) k_sub_products(const DevGraph g, FloodPlanDev F,
+                                                      const float *__restrict__ a2v_vm)
 {
     if (*(volatile const int *)F.done) return;
-    const int c = blockIdx.x;
-    const int4 ch = __ldg(F.hub + c);  // {var, begin, end, first sub-chunk of this chunk}
-    if (var_frozen(F, ch.x)) return;   // block-uniform
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int nsub = (ch.z - ch.y + kFloodSub - 1) / kFloodSub;
-    for (int s = threadIdx.x >> 5; s < nsub; s += nw) {
-        int e[kFloodSub / 32];
-        float r[kFloodSub / 32];
-        const int b = ch.y + s * kFloodSub;
-        const XP t = sub_chunk_product(g, a2v, b, min(ch.z, b + kFloodSub), lane, e, r);
-        if (lane == 0) F.agg[ch.w + s] = t;
-    }
-}
-
-// Variables of degree 1 and 2 (most of a derivation graph: every rule's
-// derivation variable has degree 2): one thread each, few registers.
-__global__ void __launch_bounds__(256) k_v2a_lean(const DevGraph g, const FloodPlanDev F,
-                                                  const float *__restrict__ a2v, float *__restrict__ v2a)
-{
-    if (*(volatile const int *)F.done) return;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv || var_frozen(F, v)) return;
-    const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
-    if (d == 0 || d > 2) return;
-    const P2 f = dec(__ldg(g.phi + v));
-    bool gd = false;
-    if (d == 1) {
-        v2a[__ldg(g.vedge + lo)] = enc_fast(f, gd);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F.n_subs) return;
+    const int4 sc = __ldg(F.subs + k);  // {variable, begin, end, agg slot or -1}
+    if (var_frozen(F, sc.x)) return;
+    XP t = seq_product(a2v_vm, sc.y, sc.z);
+    if (sc.w >= 0) {
+        F.agg[sc.w] = t;
         return;
     }
-    const int e0 = __ldg(g.vedge + lo), e1 = __ldg(g.vedge + lo + 1);
-    const P2 x0 = dec(__ldg(a2v + e0)), x1 = dec(__ldg(a2v + e1));
-    v2a[e0] = enc_fast(mul(f, x1), gd);  // each message is phi times the other one
-    v2a[e1] = enc_fast(mul(f, x0), gd);
+    xmul(t, __ldg(g.phi + sc.x));
+    F.belief[sc.x] = belief_pack(t);
 }
 
-// The other rows, from host-built lists: degree 3..8 one thread each (prefix
-// and suffix products in registers), 9..256 one warp each (row total and
-// division), longer rows in chunks (the chunk partials combined first).
-__global__ void __launch_bounds__(256) k_v2a_rest(const DevGraph g, FloodPlanDev F,
-                                                  const float *__restrict__ a2v, float *__restrict__ v2a)
+// Beliefs.  Blocks [0, nb_vars): one thread per variable of degree <= 8;
+// then one thread per medium row; then one warp per hub row (both combine
+// sub-chunk products of k_sub_products).
+__global__ void __launch_bounds__(256) k_beliefs(const DevGraph g, FloodPlanDev F, const float *__restrict__ a2v_vm)
 {
     if (*(volatile const int *)F.done) return;
     const int b = blockIdx.x;
-    if (b < F.nb_small) {
-        const int i = b * blockDim.x + threadIdx.x;
-        if (i >= F.n_small) return;
-        const int v = __ldg(F.small + i);
-        if (var_frozen(F, v)) return;
+    if (b < F.nb_vars) {
+        const int v = b * blockDim.x + threadIdx.x;
+        if (v >= g.nv || var_frozen(F, v)) return;
         const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
-        const P2 f = dec(__ldg(g.phi + v));
-        bool gd = false;
-        int e[kFloodSmallMax];
-        P2 x[kFloodSmallMax], pre[kFloodSmallMax];
-#pragma unroll
-        for (int u = 0; u < kFloodSmallMax; ++u) e[u] = u < d ? __ldg(g.vedge + lo + u) : 0;
-#pragma unroll
-        for (int u = 0; u < kFloodSmallMax; ++u) x[u] = dec(u < d ? __ldg(a2v + e[u]) : 1.f);
-        P2 acc = f;
-#pragma unroll
-        for (int u = 0; u < kFloodSmallMax; ++u) {
-            if (u < d) {  // the list is sorted by degree, so d is nearly uniform in a warp
-                pre[u] = acc;
-                acc = mul(acc, x[u]);
-                resc(acc);
-            }
-        }
-        P2 suf{1.f, 1.f};
-#pragma unroll
-        for (int u = kFloodSmallMax - 1; u >= 0; --u) {
-            if (u < d) {
-                P2 m = mul(pre[u], suf);
-                resc(m);
-                v2a[e[u]] = enc_fast(m, gd);
-                suf = mul(suf, x[u]);
-                resc(suf);
-            }
-        }
-        return;
-    }
-    const int bm = b - F.nb_small;
-    if (bm < F.nb_medium) {
-        // one warp per variable of degree in (kFloodSmallMax, kFloodMediumMax]:
-        // the row is a single sub-chunk
-        const int w = bm * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-        if (w >= F.n_medium) return;
-        const int v = __ldg(F.medium + w);
-        if (var_frozen(F, v)) return;
-        const int lo = __ldg(g.vptr + v), hi = __ldg(g.vptr + v + 1);
-        int e[kFloodSub / 32];
-        float r[kFloodSub / 32];
-        const XP t = sub_chunk_product(g, a2v, lo, hi, lane, e, r);
+        if (d > kFloodSmallMax) return;  // a row of sub-chunks
         const float phi = __ldg(g.phi + v);
+        // slots past the warp's longest row are skipped by a uniform branch
+        // (a padded slot would multiply by exactly 1)
+        const int dw = __reduce_max_sync(__activemask(), d);
+        float r[kFloodSmallMax];
 #pragma unroll
-        for (int u = 0; u < kFloodSub / 32; ++u)
-            if (e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
+        for (int u = 0; u < kFloodSmallMax / 2; ++u) r[u] = u < d ? __ldg(a2v_vm + lo + u) : 1.f;
+        if (dw > kFloodSmallMax / 2) {
+#pragma unroll
+            for (int u = kFloodSmallMax / 2; u < kFloodSmallMax; ++u) r[u] = u < d ? __ldg(a2v_vm + lo + u) : 1.f;
+        }
+        XP t = xp_one();
+#pragma unroll
+        for (int u = 0; u < kFloodSmallMax; ++u)
+            if (u < dw) xmul(t, r[u]);
+        xmul(t, phi);
+        F.belief[v] = belief_pack(t);
         return;
     }
-    // hub chunk: combine the row's sub-chunk partials (canonical grouping),
-    // then every entry of this chunk
-    const int c = bm - F.nb_medium;
-    const int4 ch = __ldg(F.hub + c);
-    if (var_frozen(F, ch.x)) return;  // block-uniform
-    const int2 rs = __ldg(F.hub_row + c);  // {first sub-chunk of the row, sub-chunks of the row}
-    __shared__ XP s_tot;
-    if (threadIdx.x < 32) {
-        XP t = xp_one();
-        for (int j = threadIdx.x; j < rs.y; j += 32) t = xcombine(t, F.agg[rs.x + j]);
-        t = warp_product(t);
-        if (threadIdx.x == 0) s_tot = t;
+    if (b < F.nb_vars + F.nb_medium) {
+        const int w = (b - F.nb_vars) * blockDim.x + threadIdx.x;
+        if (w >= F.n_medium) return;
+        const int4 row = __ldg(F.medium + w);  // {variable, first agg slot, sub-chunks (2..8), 0}
+        if (var_frozen(F, row.x)) return;
+        const XP *P = F.agg + row.y;
+        const int ns = row.z;
+        // the butterfly over 32 slots of which slots 0..ns-1 hold sub-chunk
+        // products (the others the identity): slot 0 ends with
+        // ((P0 P4)(P2 P6)) ((P1 P5)(P3 P7)); a product with the identity is
+        // the value itself, so missing sub-chunks are skipped
+        XP t = P[0];
+        if (ns > 4) t = xcombine(t, P[4]);
+        if (ns > 2) {
+            XP u = P[2];
+            if (ns > 6) u = xcombine(u, P[6]);
+            t = xcombine(t, u);
+        }
+        XP u = P[1];
+        if (ns > 5) u = xcombine(u, P[5]);
+        if (ns > 3) {
+            XP u3 = P[3];
+            if (ns > 7) u3 = xcombine(u3, P[7]);
+            u = xcombine(u, u3);
+        }
+        t = xcombine(t, u);
+        xmul(t, __ldg(g.phi + row.x));
+        F.belief[row.x] = belief_pack(t);
+        return;
     }
-    __syncthreads();
-    const XP t = s_tot;
-    const float phi = __ldg(g.phi + ch.x);
-    for (int k0 = ch.y + threadIdx.x; k0 < ch.z; k0 += 4 * blockDim.x) {
-        int e[4];
-        float r[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = k0 + u * blockDim.x < ch.z ? __ldg(g.vedge + k0 + u * blockDim.x) : -1;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) r[u] = e[u] >= 0 ? __ldg(a2v + e[u]) : 1.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (e[u] >= 0) v2a[e[u]] = excl_msg(t, phi, r[u]);
+    const int hr = (b - F.nb_vars - F.nb_medium) * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (hr >= F.n_hub_rows) return;
+    const int4 row = __ldg(F.hub_row + hr);  // {variable, first agg slot, sub-chunks, 0}
+    if (var_frozen(F, row.x)) return;
+    XP t = xp_one();
+    for (int j = lane; j < row.z; j += 32) t = xcombine(t, F.agg[row.y + j]);
+    t = warp_product(t);
+    if (lane == 0) {
+        xmul(t, __ldg(g.phi + row.x));
+        F.belief[row.x] = belief_pack(t);
     }
 }
 
@@ -329,46 +343,204 @@ __device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph,
     if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) max_bits(F.batch.res + graph, bits);
 }
 
-// One lane per message: each warp holds whole factors (consecutive in the
-// factor-major order, so its edges are one contiguous range and every load
-// and the store are coalesced).  A lane reads its own incoming v->a message;
-// the factor's other messages come from the neighbouring lanes by shuffle, in
-// premise order (the order of a2v_unified, so the arithmetic is the level
-// engine's), over a trip count that is uniform in the warp, so that factors of
-// different types and fan-ins in one warp run one instruction stream.  A
-// factor of at most 32 variables has Ps <= 2^31, so the products need no
-// rescaling here.  The a->v messages are written in place: phase 2 reads only
-// v->a messages.
-__global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const FloodPlanDev F,
-                                                   const float *__restrict__ v2a, float *__restrict__ a2v, IterCtl ctl)
+// Typed factors of at most K variables, one thread per factor (all factors
+// by id for K = 4, the factors of a list for K = 8).  The closed forms (Eq. 4
+// with the common products factored out) need, for each target, three
+// products over the factor's other premises:
+//   X = prod m_j1,  Y = prod s_j (s_j = m_j0 + m_j1),
+//   D = sum_k (prod_{j<k} m_j1) m_k0 (prod_{j>k} s_j)  (= Y - X, no cancellation),
+// which compose over concatenated runs of premises as
+//   (X, Y, D)_LR = (X_L X_R, Y_L Y_R, D_L Y_R + X_L D_R),
+// so each target's products are its prefix run composed with its suffix run.
+// With the output's incoming message my and p the factor's parameter (q = 1-p):
+//   type         to the output             to a premise
+//   AND          (D, X)                    (my0 Y, my1 X + my0 D)
+//   NOISY_AND    (qX + D, pX)              (my0 Y, (p my1 + q my0) X + my0 D)
+//   NOISY_IMPLY  (qX + D, pX + D)          (sy Y, (p my1 + q my0) X + sy D), sy = my0 + my1
+//   PRIOR        NOISY_AND with no premise: (q, p)
+//   OR           AND with every incoming message and the result flipped
+//                (x -> 1-x is a bijection that maps OR onto AND)
+//   NOT          AND with one premise and the result flipped
+//   EQ           every variable is a "premise", s_j replaced by m_j0:
+//                to variable i (Y, X) = (prod_{u != i} m_u0, prod_{u != i} m_u1)
+// Messages enter scaled so that their larger entry is 1, so Y <= 2^K.  The
+// K slots are registers (every load is issued first); slots past the
+// warp's largest factor are skipped by a uniform branch.
+template <int K>
+__global__ void __launch_bounds__(256) k_a2v_thread(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
+                                                    float *__restrict__ a2v_vm, IterCtl ctl, const int32_t *list,
+                                                    int n_items)
 {
     if (*(volatile const int *)F.done) return;
-    __shared__ float s_x[256];  // the lanes' incoming messages (generic factors read them here)
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float dmax = 0.f;
+    unsigned long long ng = 0;
+    int graph = -1;
+    int a = -1, lo = 0, n = 0, type = kTypeTERMS;
+    if (k < n_items) {
+        a = list ? __ldg(list + k) : k;
+        lo = __ldg(g.fptr + a);
+        n = __ldg(g.fptr + a + 1) - lo;
+        type = __ldg(g.ftype + a);
+    }
+    bool go = a >= 0 && n <= K && type != kTypeTERMS;
+    if (go && F.batch.n_graphs > 0) {
+        graph = __ldg(F.fgraph + a);
+        go = __ldcg(F.batch.done + graph) == 0;
+    }
+    if (!go) n = 0;
+    const float p = go ? __ldg(g.fparam + a) : 0.f, q = 1.f - p;
+    int slot[K];
+    float old[K], x[K];
+    const int nw = __reduce_max_sync(0xffffffffu, n);
+    {
+        int v[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            v[u] = u < n ? __ldcs(g.fvars + lo + u) : 0;
+            slot[u] = u < n ? __ldcs(F.vpos + lo + u) : 0;
+            old[u] = u < n ? __ldcs(a2v + lo + u) : 1.f;
+        }
+        uint2 bl[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) bl[u] = u < n ? __ldg(F.belief + v[u]) : make_uint2(0x3f800000u, 0u);
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (u < nw) x[u] = v2a_from_belief(bl[u], old[u]);
+    }
+    const bool eq = type == kTypeEQ, fin = type == kTypeOR, fout = type == kTypeOR || type == kTypeNOT;
+    const int np = eq ? n : n - 1;  // variables in the products: premises (EQ: all)
+    P2 my{1.f, 1.f};
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+        if (u < nw && u == n - 1 && !eq) my = dec(x[u]);
+    if (fin) my = P2{my.m1, my.m0};
+    const bool nz = type == kTypeNOISY_AND || type == kTypePRIOR, ni = type == kTypeNOISY_IMPLY;
+    const float sy = my.m0 + my.m1, w = fmaf(p, my.m1, q * my.m0);
+    // to the output: mu0 = a0 X + D, mu1 = b0 X + b1 D
+    const float a0 = (nz || ni) ? q : 0.f, b0 = (nz || ni) ? p : 1.f, b1 = ni ? 1.f : 0.f;
+    // to a premise: mu0 = c0 Y, mu1 = d0 X + d1 D
+    const float c0 = eq ? 1.f : ni ? sy : my.m0;
+    const float d0 = eq ? 1.f : (nz || ni) ? w : my.m1;
+    const float d1 = eq ? 0.f : ni ? sy : my.m0;
+    auto elem = [&](float r, float &ex, float &ey, float &ed) {
+        P2 m = dec(r);
+        if (fin) m = P2{m.m1, m.m0};
+        ex = m.m1;
+        ed = m.m0;
+        ey = eq ? m.m0 : m.m0 + m.m1;
+    };
+    // prefix runs: pX[u], pY[u], pD[u] over the premises before slot u
+    float pX[K + 1], pY[K + 1], pD[K + 1];
+    pX[0] = 1.f;
+    pY[0] = 1.f;
+    pD[0] = 0.f;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        if (u < nw) {
+            float ex, ey, ed;
+            elem(x[u], ex, ey, ed);
+            if (u >= np) ex = ey = 1.f, ed = 0.f;  // the output (or no variable): the identity
+            pX[u + 1] = pX[u] * ex;
+            pY[u + 1] = pY[u] * ey;
+            pD[u + 1] = fmaf(pD[u], ey, pX[u] * ed);
+        }
+    }
+    // suffix run from the last premise down; slot u's message is its prefix
+    // run composed with the suffix run, or (u = np) the output's
+    float sX = 1.f, sY = 1.f, sD = 0.f;
+#pragma unroll
+    for (int u = K - 1; u >= 0; --u) {
+        if (u < nw) {
+            const float X = pX[u] * sX, Y = pY[u] * sY, D = fmaf(pD[u], sY, pX[u] * sD);
+            P2 mu = u == np ? P2{fmaf(a0, X, D), fmaf(b0, X, b1 * D)} : P2{c0 * Y, fmaf(d0, X, d1 * D)};
+            if (fout) mu = P2{mu.m1, mu.m0};
+            if (u < n && (!F.elevel || __ldg(F.elevel + lo + u) == F.level)) {
+                bool gd = false;
+                const float r = enc_fast(mu, gd);
+                ng += gd;
+                const float dd = delta_p1_fast(r, old[u]);
+                dmax = fmaxf(dmax, dd);
+                __stcs(a2v + lo + u, r);
+                a2v_vm[slot[u]] = r;
+                if (F.dres) F.dres[lo + u] = dd;
+            }
+            if (u < np) {
+                float ex, ey, ed;
+                elem(x[u], ex, ey, ed);
+                sD = fmaf(ed, sY, ex * sD);
+                sX *= ex;
+                sY *= ey;
+            }
+        }
+    }
+    if (ng) atomicAdd(ctl.guards, ng);
+    if (F.batch.n_graphs > 0) {
+        batch_residual(F, graph, dmax);
+        return;
+    }
+    const float bm = block_max(dmax);
+    if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
+}
+
+// Generic factors: one lane per message; each warp holds whole factors (consecutive in the
+// factor-major order, so its edges are one contiguous range and every
+// streamed load and store is coalesced).  The warp reads its factors' row
+// offsets, types and parameters once (lane j: factor j) and each lane finds
+// its factor from the mask of factor starts.  A lane forms its own v->a
+// message from its variable's belief and its edge's current a->v message;
+// the factor's other messages come from the neighbouring lanes by shuffle, in
+// premise order (the order of a2v_unified, so the closed form's arithmetic is
+// the level engine's), over a trip count that is uniform in the warp, so that
+// factors of different types and fan-ins in one warp run one instruction
+// stream.  A factor of at most 32 variables has Ps <= 2^31, so the products
+// need no rescaling here.
+__global__ void __launch_bounds__(256) k_a2v_fused(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
+                                                   float *__restrict__ a2v_vm, IterCtl ctl)
+{
+    if (*(volatile const int *)F.done) return;
+    __shared__ float s_x[256];  // the lanes' v->a messages (generic factors read them here)
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     float d = 0.f;
     unsigned long long ng = 0;
     int graph = -1;
     if (w < F.n_warps) {  // warp-uniform
         const int4 wr = __ldg(F.warps + w);  // {first edge, end edge, first factor, end factor}
-        const int e = wr.x + lane;
-        const bool valid = e < wr.y;
-        int lo = wr.x, n = 1, type = 0, a = 0;
-        float p = 0.f, x = 1.f, old = 1.f;
-        bool frozen = false;
-        if (valid) {
-            a = __ldg(g.efac + e);
-            lo = __ldg(g.fptr + a);
-            n = __ldg(g.fptr + a + 1) - lo;
-            type = __ldg(g.ftype + a);
-            p = __ldg(g.fparam + a);
-            x = __ldg(v2a + e);
-            old = a2v[e];
-            if (F.batch.n_graphs > 0) {
-                graph = __ldg(F.fgraph + a);
-                frozen = __ldcg(F.batch.done + graph) != 0;
-            }
+        const int nf = wr.w - wr.z, ne_w = wr.y - wr.x;
+        int fst = 0, ftyp = 0, fgr = -1;
+        float fpar = 0.f;
+        if (lane < nf) {
+            fst = __ldg(g.fptr + wr.z + lane) - wr.x;
+            ftyp = __ldg(g.ftype + wr.z + lane);
+            fpar = __ldg(g.fparam + wr.z + lane);
+            if (F.batch.n_graphs > 0) fgr = __ldg(F.fgraph + wr.z + lane);
         }
-        const int first = lo - wr.x, i = e - lo, y = n - 1;
+        const unsigned starts = __reduce_or_sync(0xffffffffu, lane < nf ? 1u << fst : 0u);
+        const unsigned upto = starts & (0xffffffffu >> (31 - lane));  // factor starts at or before this lane
+        const int fi = __popc(upto) - 1;                              // this lane's factor in the warp
+        const int first = 31 - __clz(upto);                           // lane of its first edge
+        const unsigned after = starts & ~(0xffffffffu >> (31 - lane));
+        const bool valid = lane < ne_w;
+        const int n = (after ? __ffs(after) - 1 : ne_w) - first;
+        const int i = lane - first, y = n - 1;
+        const int type = __shfl_sync(0xffffffffu, ftyp, fi);
+        const float p = __shfl_sync(0xffffffffu, fpar, fi);
+        const int e = wr.x + lane;
+        float x = 1.f, old = 1.f;
+        int slot = 0;
+        bool frozen = false;
+        if (F.batch.n_graphs > 0) {
+            graph = __shfl_sync(0xffffffffu, fgr, fi);
+            frozen = graph < 0 || __ldcg(F.batch.done + graph) != 0;
+        }
+        if (valid) {
+            const int v = __ldcs(g.fvars + e);
+            slot = __ldcs(F.vpos + e);
+            old = __ldcs(a2v + e);
+            x = v2a_from_belief(__ldg(F.belief + v), old);
+        } else {
+            graph = -1;
+        }
         const int span = __reduce_max_sync(0xffffffffu, valid ? y : 0);
         Acc5 A;
         for (int j = 0; j < span; ++j) {
@@ -389,13 +561,15 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
         const bool write = valid && !frozen && (!F.elevel || __ldg(F.elevel + e) == F.level);
         if (write) {
             const float *wx = s_x + (threadIdx.x & ~31) + first;
+            const int a = wr.z + fi;
             const P2 mu = type == kTypeTERMS ? a2v_terms(g, a, n, i, [&](int j) { return dec(wx[j]); })
                                              : a2v_finish(type, p, i == y, A, dec(ry));
             bool gd = false;
             const float r = enc_fast(mu, gd);
             ng += gd;
             d = delta_p1_fast(r, old);
-            a2v[e] = r;
+            __stcs(a2v + e, r);
+            a2v_vm[slot] = r;
             if (F.dres) F.dres[e] = d;
         }
     }
@@ -408,10 +582,22 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
     if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
+// v->a messages of the edges of factors wider than a warp, formed before
+// their a->v messages are (those are written in place).
+__global__ void __launch_bounds__(256) k_wide_v2a(const DevGraph g, const FloodPlanDev F,
+                                                  const float *__restrict__ a2v)
+{
+    if (*(volatile const int *)F.done) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F.n_wide) return;
+    const int e = __ldg(F.wide + k);
+    F.wide_v2a[k] = v2a_from_belief(__ldg(F.belief + __ldg(g.fvars + e)), a2v[e]);
+}
+
 // Factors wider than a warp: one thread per edge, the closed form over the
-// factor's v->a messages read from memory.
-__global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodPlanDev F,
-                                                  const float *__restrict__ v2a, float *__restrict__ a2v, IterCtl ctl)
+// factor's v->a messages (consecutive in wide_v2a, factor by factor).
+__global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
+                                                  float *__restrict__ a2v_vm, IterCtl ctl)
 {
     if (*(volatile const int *)F.done) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -422,19 +608,23 @@ __global__ void __launch_bounds__(256) k_a2v_wide(const DevGraph g, const FloodP
         const int e = __ldg(F.wide + k);
         const int a = __ldg(g.efac + e);
         const int lo = __ldg(g.fptr + a), n = __ldg(g.fptr + a + 1) - lo;
+        const float *xv = F.wide_v2a + (k - (e - lo));  // the factor's first edge in the wide list
         bool frozen = false;
         if (F.batch.n_graphs > 0) {
             graph = __ldg(F.fgraph + a);
             frozen = __ldcg(F.batch.done + graph) != 0;
         }
         if (!frozen && (!F.elevel || __ldg(F.elevel + e) == F.level)) {
-            const P2 mu = a2v_unified(__ldg(g.ftype + a), __ldg(g.fparam + a), n, e - lo,
-                                      [&](int j) { return dec(__ldg(v2a + lo + j)); });
+            const int type = __ldg(g.ftype + a);
+            const P2 mu = type == kTypeTERMS
+                              ? a2v_terms(g, a, n, e - lo, [&](int j) { return dec(xv[j]); })
+                              : a2v_unified(type, __ldg(g.fparam + a), n, e - lo, [&](int j) { return dec(xv[j]); });
             bool gd = false;
             const float r = enc_fast(mu, gd);
             ng += gd;
             d = delta_p1_fast(r, a2v[e]);
             a2v[e] = r;
+            a2v_vm[__ldg(F.vpos + e)] = r;
             if (F.dres) F.dres[e] = d;
         }
     }
@@ -503,34 +693,43 @@ __global__ void k_flood_check(unsigned *slots, unsigned *hist, float tol, int *c
     }
 }
 
+// Phase 1 and phase 2 of one iteration (or one RESIDUAL level).
+void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a2v_vm, IterCtl ctl, cudaStream_t s)
+{
+    if (P.n_subs > 0) k_sub_products<<<(P.n_subs + P.sub_threads - 1) / P.sub_threads, P.sub_threads, 0, s>>>(g, P, a2v_vm);
+    const int nb = P.nb_vars + P.nb_medium + (P.n_hub_rows + 7) / 8;
+    if (nb > 0) k_beliefs<<<nb, 256, 0, s>>>(g, P, a2v_vm);
+    if (P.n_wide > 0) k_wide_v2a<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v);
+    if (g.na > 0) k_a2v_thread<4><<<(g.na + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl, nullptr, g.na);
+    if (P.n_fac8 > 0)
+        k_a2v_thread<8><<<(P.n_fac8 + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl, P.fac8, P.n_fac8);
+    if (P.n_warps > 0) k_a2v_fused<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
+    if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
+}
+
 }  // namespace
 
-void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+void flood_sync(const DevGraph &g, const float *a2v, float *a2v_vm, cudaStream_t s)
+{
+    if (g.ne > 0) k_sync_vm<<<(g.ne + 255) / 256, 256, 0, s>>>(g, a2v, a2v_vm);
+}
+
+void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, float tol,
                      unsigned *hist, int *done, cudaStream_t s)
 {
     FloodPlanDev P = F;
     P.done = done;
-    if (g.nv > 0) k_v2a_lean<<<(g.nv + 255) / 256, 256, 0, s>>>(g, P, a2v, v2a);
-    if (P.n_hub > 0) k_hub_partials<<<P.n_hub, 256, 0, s>>>(g, P, a2v);
-    const int nb = P.nb_small + P.nb_medium + P.n_hub;
-    if (nb > 0) k_v2a_rest<<<nb, 256, 0, s>>>(g, P, a2v, v2a);
-    if (P.n_warps > 0) k_a2v_lanes<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, v2a, a2v, ctl);
-    if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+    flood_phases(g, P, a2v, a2v_vm, ctl, s);
     if (P.batch.n_graphs > 0) k_flood_batch_check<<<1, 1024, 0, s>>>(P.batch, done);
     else k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, tol, done);
 }
 
-void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, int *done,
+void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, int *done,
                  cudaStream_t s)
 {
     FloodPlanDev P = F;
     P.done = done;
-    if (g.nv > 0) k_v2a_lean<<<(g.nv + 255) / 256, 256, 0, s>>>(g, P, a2v, v2a);
-    if (P.n_hub > 0) k_hub_partials<<<P.n_hub, 256, 0, s>>>(g, P, a2v);
-    const int nb = P.nb_small + P.nb_medium + P.n_hub;
-    if (nb > 0) k_v2a_rest<<<nb, 256, 0, s>>>(g, P, a2v, v2a);
-    if (P.n_warps > 0) k_a2v_lanes<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, v2a, a2v, ctl);
-    if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, v2a, a2v, ctl);
+    flood_phases(g, P, a2v, a2v_vm, ctl, s);
 }
 
 void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t s)
@@ -538,7 +737,7 @@ void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t
     k_flood_check<<<1, kResSlots, 0, s>>>(ctl.res, hist, tol, done);
 }
 
-cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, float tol,
                           unsigned *hist, int *done, int iters, cudaGraphExec_t *exec)
 {
     cudaStream_t cap = nullptr;
@@ -547,7 +746,7 @@ cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, 
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int k = 0; k < iters; ++k) flood_iteration(g, F, a2v, v2a, ctl, tol, hist, done, cap);
+        for (int k = 0; k < iters; ++k) flood_iteration(g, F, a2v, a2v_vm, ctl, tol, hist, done, cap);
         const cudaError_t launch = cudaGetLastError();
         e = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess && launch != cudaSuccess) e = launch;
@@ -560,8 +759,8 @@ cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, 
 
 int flood_launches(const DevGraph &g, const FloodPlanDev &F)
 {
-    return (g.nv > 0) + (F.n_hub > 0) + (F.nb_small + F.nb_medium + F.n_hub > 0) + (F.n_warps > 0) +
-           (F.n_wide > 0) + 1;
+    return (F.n_subs > 0) + (F.nb_vars + F.nb_medium + F.n_hub_rows > 0) + 2 * (F.n_wide > 0) + (g.na > 0) + (F.n_fac8 > 0) +
+           (F.n_warps > 0) + 1;
 }
 
 }  // namespace fbp

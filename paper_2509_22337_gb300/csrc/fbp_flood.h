@@ -13,31 +13,45 @@ struct XP {
     int z0, z1;
 };
 
-constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread each
-constexpr int kFloodMediumMax = 256;   // rows up to this degree: one warp each
-constexpr int kFloodHubChunk = 1024;   // longer rows: chunks of this many entries (one block)
-constexpr int kFloodSub = 256;         // the grouping unit of a long row's product (= kFloodMediumMax)
-static_assert(kFloodSub == kFloodMediumMax, "a warp-per-row row is exactly one sub-chunk");
-static_assert(kFloodHubChunk % kFloodSub == 0, "chunks hold whole sub-chunks");
+constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread each, in row order
+constexpr int kFloodSub = 32;          // the grouping unit of a longer row's product
+constexpr int kFloodMediumMax = 256;   // rows up to this degree may combine in one thread
+static_assert(kFloodMediumMax <= 8 * kFloodSub, "a medium row has at most 8 sub-chunks");
+constexpr int kFloodChunkUnit = 256;   // FBP_OPT_FLOOD_CHUNK is a multiple of this many entries
+constexpr int kFloodHubChunk = 8192;   // entries per block of the sub-chunk pass (default)
+static_assert(kFloodHubChunk % kFloodChunkUnit == 0 && kFloodChunkUnit % kFloodSub == 0, "whole sub-chunks");
 constexpr int kFloodChunk = 8;         // iterations per captured CUDA graph
 
 struct FloodPlanDev {
-    int32_t nb_small = 0;              // blocks of the one-thread-per-row role (degree 3..8)
-    int32_t n_small = 0;
-    const int32_t *small = nullptr;    // [n_small] variables of degree 3..8
-    int32_t nb_medium = 0;             // blocks of the warp-per-row role
+    // phase 1 (beliefs, variable-major): every variable of degree <= 8 one
+    // thread (blocks 0 .. nb_vars-1); every longer row in 32-entry
+    // sub-chunks, one thread each (a row of one sub-chunk writes its belief
+    // there); then one thread per medium row (2..8 sub-chunks) or one warp per
+    // hub row combines the sub-chunk products
+    int32_t nb_vars = 0;
+    int32_t n_subs = 0;
+    const int4 *subs = nullptr;        // [n_subs] {variable, begin, end, agg slot or -1: the row's only one}
+    int32_t sub_threads = 0;           // threads per block of the sub-chunk pass
+    int32_t nb_medium = 0;             // blocks of the thread-per-medium-row role
     int32_t n_medium = 0;
-    const int32_t *medium = nullptr;   // [n_medium] variables of medium degree
-    int32_t n_hub = 0;                 // hub chunks
-    const int4 *hub = nullptr;         // [n_hub] {variable, chunk begin, chunk end, first sub-chunk of the chunk}
-    const int2 *hub_row = nullptr;     // [n_hub] {first sub-chunk of the chunk's row, sub-chunks of the row}
-    XP *agg = nullptr;                 // [sub-chunks of all hub rows] partial product of each sub-chunk
-    // phase 2: warps of whole consecutive factors; factors wider than a warp
-    // edge by edge
+    const int4 *medium = nullptr;      // [n_medium] {variable, first agg slot, sub-chunks, 0}, by sub-chunk count
+    int32_t n_hub_rows = 0;
+    const int4 *hub_row = nullptr;     // [n_hub_rows] {variable, first agg slot, sub-chunks, 0}
+    XP *agg = nullptr;                 // product of each sub-chunk of a row of several
+    uint2 *belief = nullptr;           // [nv] belief record of each variable (see fbp_flood.cu)
+    // phase 2 (factor-major): typed factors of at most 4 variables one thread
+    // each, by factor id; typed factors of 5..8 variables one thread each,
+    // from a list; runs of consecutive other factors of at most 32 variables
+    // (generic ones, typed ones of 9..32) in warps of whole factors; factors
+    // wider than a warp edge by edge
+    int32_t n_fac8 = 0;
+    const int32_t *fac8 = nullptr;     // [n_fac8] typed factors of 5..8 variables
     int32_t n_warps = 0;
     const int4 *warps = nullptr;       // [n_warps] {first edge, end edge, first factor, end factor}
     int32_t n_wide = 0;
-    const int32_t *wide = nullptr;     // [n_wide] edges of factors wider than a warp
+    const int32_t *wide = nullptr;     // [n_wide] edges of factors wider than a warp, factor by factor
+    float *wide_v2a = nullptr;         // [n_wide] their v->a messages, formed before phase 2
+    const int32_t *vpos = nullptr;     // [ne] slot of each edge in the variable-major message copy
     const int *done = nullptr;         // set once the run has converged
     // one level of the device-scheduled RESIDUAL strategy: phase 2 writes only
     // the edges with elevel[e] == level, and records each written edge's
@@ -51,28 +65,36 @@ struct FloodPlanDev {
     BatchCtl batch;
 };
 
+// The flooding kernels keep two copies of the a->v messages: a2v in the
+// factor-major (edge id) order every other part of the library uses, and
+// a2v_vm in variable-major order (slot k of variable v's row holds the
+// message of edge vedge[k]), which phase 1 reads contiguously.  Phase 2
+// writes both.  flood_sync makes a2v_vm a copy of a2v; call it before the
+// first flooding iteration whenever a2v was written by anything else
+// (reset, import, the level engine).
+void flood_sync(const DevGraph &g, const float *a2v, float *a2v_vm, cudaStream_t s);
 // One flooding iteration: phase 1 over every variable row, phase 2 over
-// every factor (in place on a2v), then the convergence check.  done[4] is the
-// run's control block on the device: [0] 0 while running, 1 once converged
-// (or, for a batch, once no graph runs), 2 at the iteration limit; [1] the
-// last iteration executed (the device counts iterations itself, so queued or
-// captured iterations need no argument); [3] the iteration limit.
-// hist[it-1] receives iteration it's residual bits.  Every kernel returns at
-// once when done[0] is set, so iterations can be queued in batches, or
-// replayed from a captured graph, without a host synchronisation per
-// iteration.
-void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+// every factor (in place on a2v, mirrored into a2v_vm), then the convergence
+// check.  done[4] is the run's control block on the device: [0] 0 while
+// running, 1 once converged (or, for a batch, once no graph runs), 2 at the
+// iteration limit; [1] the last iteration executed (the device counts
+// iterations itself, so queued or captured iterations need no argument); [3]
+// the iteration limit.  hist[it-1] receives iteration it's residual bits.
+// Every kernel returns at once when done[0] is set, so iterations can be
+// queued in batches, or replayed from a captured graph, without a host
+// synchronisation per iteration.
+void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, float tol,
                      unsigned *hist, int *done, cudaStream_t s);
 // The two phases of one level of a device-scheduled RESIDUAL iteration
-// (F.elevel, F.level, F.dres set): every v->a message from the level-start
-// state, then the level's a->v messages.  No convergence check.
-void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, int *done,
+// (F.elevel, F.level, F.dres set): every belief from the level-start state,
+// then the level's a->v messages.  No convergence check.
+void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, int *done,
                  cudaStream_t s);
 // End of a device-scheduled RESIDUAL iteration: the check of flood_iteration.
 void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t s);
 // A CUDA graph of `iters` consecutive flood_iterations (captured on a private
 // stream; launch it on any stream).
-cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *v2a, IterCtl ctl, float tol,
+cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, float tol,
                           unsigned *hist, int *done, int iters, cudaGraphExec_t *exec);
 // Kernel launches of one flood_iteration.
 int flood_launches(const DevGraph &g, const FloodPlanDev &F);

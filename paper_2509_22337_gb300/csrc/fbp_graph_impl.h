@@ -41,7 +41,7 @@ struct fbp_graph {
     // messages
     float *a2v[2] = {nullptr, nullptr};
     int cur = 0;
-    float *v2a = nullptr;
+    float *a2v_vm = nullptr;          // flooding: variable-major copy of the a->v messages [E]
     float *pairs = nullptr;           // export/import staging [2E]
     float *p1 = nullptr;              // marginals [V]
     // schedule

@@ -174,107 +174,117 @@ int upload_erow(fbp_graph *g)
     return upload(g, &g->erow, er.data(), er.size());
 }
 
-// Flooding plan: variables by degree class (one thread / one warp per row,
-// or chunks of a hub row), and the shared-memory staging size of phase 2.
+// Flooding plan: variables by degree class (every row of degree <= 8 one
+// thread, medium rows one warp each, hub rows in chunks), the slot of every
+// edge in the variable-major message copy, and phase 2's warps of whole
+// factors.
 int build_flood_plan(fbp_graph *g)
 {
     const HostCSR &h = g->h;
     flood_exec_drop(g);
     if (g->flood_ready) {  // a rebuild after retuning
-        dfree(g, (void *)g->flood.small);
+        dfree(g, (void *)g->flood.subs);
         dfree(g, (void *)g->flood.medium);
-        dfree(g, (void *)g->flood.hub);
         dfree(g, (void *)g->flood.hub_row);
         dfree(g, (void *)g->flood.agg);
+        dfree(g, (void *)g->flood.belief);
         dfree(g, (void *)g->flood.warps);
+        dfree(g, (void *)g->flood.fac8);
         dfree(g, (void *)g->flood.wide);
+        dfree(g, (void *)g->flood.wide_v2a);
+        dfree(g, (void *)g->flood.vpos);
         g->flood = FloodPlanDev{};
         g->flood_ready = false;
     }
     FloodPlanDev F;
-    std::vector<int32_t> small, medium;
-    std::vector<int4> hub;
-    std::vector<int2> hub_row;
-    int32_t n_sub = 0;  // sub-chunks of all hub rows so far
+    std::vector<int4> subs, medium, hub_row;
+    int32_t n_agg = 0;  // sub-chunk products of rows of several sub-chunks
     for (int32_t v = 0; v < h.nv; ++v) {
         const int32_t lo = h.vptr[v], hi = h.vptr[v + 1], d = hi - lo;
-        if (d <= 2) continue;  // the lean kernel's rows
-        if (d <= kFloodSmallMax) {
-            small.push_back(v);
-            continue;
-        }
-        if (d <= g->flood_hub_min) {
-            medium.push_back(v);
-            continue;
-        }
-        const int32_t ch = g->flood_chunk;  // a multiple of kFloodSub
-        const int32_t nc = (d + ch - 1) / ch, ns = (d + kFloodSub - 1) / kFloodSub;
-        for (int32_t c = 0; c < nc; ++c) {
-            hub.push_back(make_int4(v, lo + c * ch, std::min(hi, lo + (c + 1) * ch), n_sub + c * (ch / kFloodSub)));
-            hub_row.push_back(make_int2(n_sub, ns));
-        }
-        n_sub += ns;
+        if (d <= kFloodSmallMax) continue;  // the one-thread rows
+        const int32_t ns = (d + kFloodSub - 1) / kFloodSub;
+        for (int32_t c = 0; c < ns; ++c)
+            subs.push_back(make_int4(v, lo + c * kFloodSub, std::min(hi, lo + (c + 1) * kFloodSub), ns == 1 ? -1 : n_agg + c));
+        if (ns == 1) continue;
+        (d <= g->flood_hub_min ? medium : hub_row).push_back(make_int4(v, n_agg, ns, 0));
+        n_agg += ns;
     }
-    // rows of one degree side by side: the per-row loops of a warp then run
-    // to nearly the same length (each row is independent: same results)
-    std::stable_sort(small.begin(), small.end(), [&h](int32_t a, int32_t b) {
-        return h.vptr[a + 1] - h.vptr[a] < h.vptr[b + 1] - h.vptr[b];
+    // rows of one sub-chunk count side by side: the combines of a warp then
+    // run the same branches (each row is independent: same results)
+    std::stable_sort(medium.begin(), medium.end(), [](const int4 &a, const int4 &b) { return a.z < b.z; });
+    // slot of each edge in the variable-major copy: the inverse of vedge
+    std::vector<int32_t> vpos(h.ne);
+    parallel_for(h.ne, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t k = b; k < e; ++k) vpos[h.vedge[k]] = (int32_t)k;
     });
-    std::stable_sort(medium.begin(), medium.end(), [&h](int32_t a, int32_t b) {
-        return h.vptr[a + 1] - h.vptr[a] < h.vptr[b + 1] - h.vptr[b];
-    });
-    F.n_small = (int32_t)small.size();
-    F.nb_small = (F.n_small + 255) / 256;
+    F.nb_vars = (h.nv + 255) / 256;
+    F.n_subs = (int32_t)subs.size();
+    F.sub_threads = std::max(32, std::min(256, g->flood_chunk / kFloodSub));
     F.n_medium = (int32_t)medium.size();
-    F.nb_medium = (F.n_medium + 7) / 8;
-    F.n_hub = (int32_t)hub.size();
-    int32_t *d_small = nullptr, *d_medium = nullptr;
-    int4 *d_hub = nullptr;
-    int2 *d_hub_row = nullptr;
+    F.nb_medium = (F.n_medium + 255) / 256;
+    F.n_hub_rows = (int32_t)hub_row.size();
+    int32_t *d_vpos = nullptr;
+    int4 *d_subs = nullptr, *d_medium = nullptr, *d_hub_row = nullptr;
     XP *d_agg = nullptr;
-    int rc = upload(g, &d_small, small.data(), small.size());
+    uint2 *d_belief = nullptr;
+    int rc = upload(g, &d_subs, subs.data(), subs.size());
     if (!rc) rc = upload(g, &d_medium, medium.data(), medium.size());
-    if (!rc) rc = upload(g, &d_hub, hub.data(), hub.size());
     if (!rc) rc = upload(g, &d_hub_row, hub_row.data(), hub_row.size());
-    if (!rc) rc = dalloc_n(g, &d_agg, std::max<size_t>(n_sub, 1));
+    if (!rc) rc = dalloc_n(g, &d_agg, std::max<size_t>(n_agg, 1));
+    if (!rc) rc = dalloc_n(g, &d_belief, std::max<size_t>(h.nv, 1));
+    if (!rc) rc = upload(g, &d_vpos, vpos.data(), vpos.size());
     if (rc) return rc;
-    F.small = d_small;
+    F.subs = d_subs;
     F.medium = d_medium;
-    F.hub = d_hub;
     F.hub_row = d_hub_row;
     F.agg = d_agg;
-    // phase 2: consecutive whole factors packed into warps of at most 32 edges;
-    // a factor wider than a warp goes edge by edge to the wide list
+    F.belief = d_belief;
+    F.vpos = d_vpos;
+    // phase 2: typed factors of at most 4 variables are found by id; typed
+    // factors of 5..8 variables are listed; runs of consecutive other factors
+    // of at most 32 variables are packed whole into warps of at most 32
+    // edges; a factor wider than a warp goes edge by edge to the wide list
     std::vector<int4> warps;
-    std::vector<int32_t> wide;
+    std::vector<int32_t> wide, fac8;
     {
-        int32_t a0 = 0;
+        int32_t a0 = 0;  // open warp: first factor
         auto close = [&](int32_t a1) {
             if (a1 > a0) warps.push_back(make_int4((int)h.fptr[a0], (int)h.fptr[a1], a0, a1));
+            a0 = a1;
         };
         for (int32_t a = 0; a < h.na; ++a) {
             const int64_t n = h.fptr[a + 1] - h.fptr[a];
+            const bool typed = h.ftype[a] != FBP_TERMS;
+            if (typed && n <= 8) {
+                close(a);
+                if (n > 4) fac8.push_back(a);
+                a0 = a + 1;
+                continue;
+            }
             if (n > 32) {
                 close(a);
                 for (int64_t e = h.fptr[a]; e < h.fptr[a + 1]; ++e) wide.push_back((int32_t)e);
                 a0 = a + 1;
                 continue;
             }
-            if (h.fptr[a + 1] - h.fptr[a0] > 32) {
-                close(a);
-                a0 = a;
-            }
+            if (h.fptr[a + 1] - h.fptr[a0] > 32) close(a);
         }
         close(h.na);
     }
     int4 *d_warps = nullptr;
-    int32_t *d_wide = nullptr;
-    if ((rc = upload(g, &d_warps, warps.data(), warps.size())) || (rc = upload(g, &d_wide, wide.data(), wide.size())))
+    int32_t *d_wide = nullptr, *d_fac8 = nullptr;
+    float *d_wide_v2a = nullptr;
+    if ((rc = upload(g, &d_fac8, fac8.data(), fac8.size())) ||
+        (rc = upload(g, &d_warps, warps.data(), warps.size())) || (rc = upload(g, &d_wide, wide.data(), wide.size())) ||
+        (rc = dalloc_n(g, &d_wide_v2a, std::max<size_t>(wide.size(), 1))))
         return rc;
+    F.n_fac8 = (int32_t)fac8.size();
+    F.fac8 = d_fac8;
     F.n_warps = (int32_t)warps.size();
     F.warps = d_warps;
     F.n_wide = (int32_t)wide.size();
     F.wide = d_wide;
+    F.wide_v2a = d_wide_v2a;
     g->flood = F;
     g->flood_ready = true;
     return FBP_OK;
@@ -928,7 +938,7 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     // flooding: a captured chunk of kFloodChunk iterations is replayed in
     // growing batches; the device counts iterations, marks the run done at
     // convergence or at the limit, and later kernels return at once
-    if (!g->v2a && dalloc_n(g, &g->v2a, (size_t)h.ne)) return FBP_ERR_OOM;
+    if (!g->a2v_vm && dalloc_n(g, &g->a2v_vm, (size_t)h.ne)) return FBP_ERR_OOM;
     if (!g->flood_ready) {
         int rc = build_flood_plan(g);
         if (rc) return rc;
@@ -938,6 +948,8 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     if (max_iters == 0) return finish_run(g, 0, 0.0, FBP_NOT_CONVERGED, iters_out, residual_out);
     cudaGraphExec_t exec = nullptr;
     if ((rc = flood_exec_for(g, g->flood, (float)tol, kFloodChunk, &exec))) return rc;
+    flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, g->stream);  // the messages may have changed since
+    g->stats.kernel_launches += h.ne > 0;
     CUDA_TRY(cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, g->stream));
     g->h_out[0] = g->h_out[1] = g->h_out[2] = 0;
     g->h_out[3] = max_iters;
@@ -971,7 +983,7 @@ int fbp::flood_exec_for(fbp_graph *g, const FloodPlanDev &F, float tol, int iter
     }
     flood_exec_drop(g);
     IterCtl ctl{g->d_res, g->d_guards};
-    CUDA_TRY(flood_capture(g->d, F, g->a2v[g->cur], g->v2a, ctl, tol, g->d_res_it, g->d_out, iters, &g->flood_exec));
+    CUDA_TRY(flood_capture(g->d, F, g->a2v[g->cur], g->a2v_vm, ctl, tol, g->d_res_it, g->d_out, iters, &g->flood_exec));
     g->flood_exec_iters = iters;
     g->flood_exec_tol = tol;
     std::copy(key, key + 3, g->flood_exec_key);
@@ -998,7 +1010,7 @@ int fbp_run_residual_device(fbp_graph *g, int32_t max_iters, double tol, int32_t
 {
     const HostCSR &h = g->h;
     int rc;
-    if (!g->v2a && (rc = dalloc_n(g, &g->v2a, (size_t)h.ne))) return rc;
+    if (!g->a2v_vm && (rc = dalloc_n(g, &g->a2v_vm, (size_t)h.ne))) return rc;
     if (!g->flood_ready && (rc = build_flood_plan(g))) return rc;
     if ((rc = ensure_res_cap(g, std::max(max_iters, 1)))) return rc;
     if (!g->dres && (rc = dalloc_n(g, &g->dres, (size_t)std::max(h.ne, 1)))) return rc;
@@ -1018,6 +1030,8 @@ int fbp_run_residual_device(fbp_graph *g, int32_t max_iters, double tol, int32_t
     FloodPlanDev F = g->flood;
     F.dres = g->dres;
     const int per_level = flood_launches(g->d, g->flood) - 1;
+    flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, g->stream);
+    g->stats.kernel_launches += h.ne > 0;
     int32_t it = 0, levels = 0;
     bool idle = false;  // no factor active
     int status = FBP_NOT_CONVERGED;
@@ -1045,7 +1059,7 @@ int fbp_run_residual_device(fbp_graph *g, int32_t max_iters, double tol, int32_t
         CUDA_TRY(cudaMemsetAsync(g->dres, 0, sizeof(float) * h.ne, g->stream));
         for (int32_t lv = 0; lv < levels; ++lv) {
             F.level = lv;
-            flood_level(g->d, F, g->a2v[g->cur], g->v2a, ctl, g->d_out, g->stream);
+            flood_level(g->d, F, g->a2v[g->cur], g->a2v_vm, ctl, g->d_out, g->stream);
             g->stats.kernel_launches += per_level;
         }
         flood_check(ctl, (float)tol, g->d_res_it, g->d_out, g->stream);
@@ -1186,8 +1200,9 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         g->flood_ready = false;  // rebuilt at the next flooding run
         return FBP_OK;
     case FBP_OPT_FLOOD_CHUNK:
-        if (value < kFloodSub || value > (1 << 16) || value % kFloodSub != 0)
-            return fail(FBP_ERR_INVALID_ARG, "chunk must be a multiple of %d in [%d, 65536]", kFloodSub, kFloodSub);
+        if (value < kFloodChunkUnit || value > (1 << 16) || value % kFloodChunkUnit != 0)
+            return fail(FBP_ERR_INVALID_ARG, "chunk must be a multiple of %d in [%d, 65536]", kFloodChunkUnit,
+                        kFloodChunkUnit);
         g->flood_chunk = (int)value;
         g->flood_ready = false;
         return FBP_OK;

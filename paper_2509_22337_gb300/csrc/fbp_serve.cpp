@@ -131,7 +131,8 @@ int64_t estimate_bytes(int64_t nv, int64_t na, int64_t ne, int32_t max_iters, in
                 8 * (nv + 1) /* vptr, phi */ + 4 * nv /* marginals */ + 4 * (int64_t)std::max(max_iters, 64) +
                 (1 << 16);
     if (strategy == FBP_PARALL)
-        b += 4 * ne /* v2a */ + 12 * nv /* degree-class lists */ + 64 * (ne / 256 + 1) /* hub chunks */;
+        b += 8 * ne /* variable-major copy, slots */ + 12 * nv /* beliefs, degree-class lists */ +
+             64 * (ne / 256 + 1) /* hub chunks */;
     else
         b += 16 * ne /* the engine's row records */ + 4 * ne /* second message buffer */ +
              2 * (3 * (16 * ne + 8 * ne) / 2 + 8 * ne) /* padded lanes, rows, (edge, level) */ +
@@ -207,7 +208,7 @@ int fbp_server::load(Sess &s)
                                s.has_factor_rank ? s.factor_rank.data() : nullptr, s.residual_buckets};
         if ((rc = fbp_schedule_set(s.g, &spec))) return rc;
     } else {
-        if (!s.g->v2a && (rc = dalloc_n(s.g, &s.g->v2a, (size_t)s.g->h.ne))) return rc;
+        if (!s.g->a2v_vm && (rc = dalloc_n(s.g, &s.g->a2v_vm, (size_t)s.g->h.ne))) return rc;
         if ((rc = build_flood_plan(s.g))) return rc;
     }
     if ((rc = ensure_res_cap(s.g, std::max(s.max_iters, 1)))) return rc;
@@ -297,6 +298,10 @@ int fbp_server::start(Sess &s, int64_t ticket)
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), s.stream);
     if (s.strategy == FBP_PARALL) {
         if (e == cudaSuccess) e = cudaMemsetAsync(g->d_res, 0, sizeof(unsigned) * kResSlots, s.stream);
+        if (e == cudaSuccess) {
+            flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, s.stream);
+            stats.kernel_launches += g->h.ne > 0;
+        }
     } else {
         if (e == cudaSuccess)
             e = cudaMemsetAsync(g->d_res_it, 0, sizeof(unsigned) * std::max(s.max_iters, 1), s.stream);

@@ -31,13 +31,10 @@
 // Phase 2, the closed-form local-structure messages (Eq. 4).  Every v->a
 // message is formed from its variable's belief and the edge's current a->v
 // message; the new a->v message is written in place (factor-major) and into
-// the variable-major copy.  Typed factors of at most 4 variables (most of a
-// derivation graph): one thread per factor over every factor id, prefix and
-// suffix products in registers; typed factors of 5..8 variables: the same
-// from a list of their ids.  Generic factors and typed factors of 9..32
-// variables: one lane per message, whole consecutive factors per warp, the
-// factor's other messages by warp shuffle.  Factors wider than a warp: one
-// thread per edge.
+// the variable-major copy.  Factors of at most 32 variables: one lane per
+// message, whole consecutive factors per warp, the factor's other messages by
+// warp shuffle (typed factors in one kernel, generic ones in another).
+// Factors wider than a warp: one thread per edge.
 //
 // Memory traffic per iteration: phase 1 streams the variable-major copy,
 // the row offsets and phi and writes one record per variable; phase 2
@@ -343,16 +340,19 @@ __device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph,
     if (graph >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1 && bits) max_bits(F.batch.res + graph, bits);
 }
 
-// Typed factors of at most K variables, one thread per factor (all factors
-// by id for K = 4, the factors of a list for K = 8).  The closed forms (Eq. 4
-// with the common products factored out) need, for each target, three
-// products over the factor's other premises:
+// Typed factors of at most 32 variables: one lane per message, each warp
+// holding whole consecutive factors (so its edges are one contiguous range and
+// every streamed load and store is coalesced).  The warp reads its factors'
+// row offsets, types and parameters once (lane j: factor j) and each lane
+// finds its factor from the mask of factor starts.  A lane forms its own v->a
+// message from its variable's belief and its edge's current a->v message; the
+// closed forms (Eq. 4 with the common products factored out) then need three
+// products over the factor's premises other than the lane's own:
 //   X = prod m_j1,  Y = prod s_j (s_j = m_j0 + m_j1),
 //   D = sum_k (prod_{j<k} m_j1) m_k0 (prod_{j>k} s_j)  (= Y - X, no cancellation),
-// which compose over concatenated runs of premises as
-//   (X, Y, D)_LR = (X_L X_R, Y_L Y_R, D_L Y_R + X_L D_R),
-// so each target's products are its prefix run composed with its suffix run.
-// With the output's incoming message my and p the factor's parameter (q = 1-p):
+// accumulated in premise order from the neighbouring lanes' messages by
+// shuffle, over a trip count that is uniform in the warp.  With the output's
+// incoming message my and p the factor's parameter (q = 1-p):
 //   type         to the output             to a premise
 //   AND          (D, X)                    (my0 Y, my1 X + my0 D)
 //   NOISY_AND    (qX + D, pX)              (my0 Y, (p my1 + q my0) X + my0 D)
@@ -363,127 +363,103 @@ __device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph,
 //   NOT          AND with one premise and the result flipped
 //   EQ           every variable is a "premise", s_j replaced by m_j0:
 //                to variable i (Y, X) = (prod_{u != i} m_u0, prod_{u != i} m_u1)
-// Messages enter scaled so that their larger entry is 1, so Y <= 2^K.  The
-// K slots are registers (every load is issued first); slots past the
-// warp's largest factor are skipped by a uniform branch.
-template <int K>
-__global__ void __launch_bounds__(256) k_a2v_thread(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
-                                                    float *__restrict__ a2v_vm, IterCtl ctl, const int32_t *list,
-                                                    int n_items)
+// Messages enter scaled so that their larger entry is 1, so Y <= 2^31.
+__global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
+                                                   float *__restrict__ a2v_vm, IterCtl ctl)
 {
     if (*(volatile const int *)F.done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    float dmax = 0.f;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    float dd = 0.f;
     unsigned long long ng = 0;
     int graph = -1;
-    int a = -1, lo = 0, n = 0, type = kTypeTERMS;
-    if (k < n_items) {
-        a = list ? __ldg(list + k) : k;
-        lo = __ldg(g.fptr + a);
-        n = __ldg(g.fptr + a + 1) - lo;
-        type = __ldg(g.ftype + a);
-    }
-    bool go = a >= 0 && n <= K && type != kTypeTERMS;
-    if (go && F.batch.n_graphs > 0) {
-        graph = __ldg(F.fgraph + a);
-        go = __ldcg(F.batch.done + graph) == 0;
-    }
-    if (!go) n = 0;
-    const float p = go ? __ldg(g.fparam + a) : 0.f, q = 1.f - p;
-    int slot[K];
-    float old[K], x[K];
-    const int nw = __reduce_max_sync(0xffffffffu, n);
-    {
-        int v[K];
-#pragma unroll
-        for (int u = 0; u < K; ++u) {
-            v[u] = u < n ? __ldcs(g.fvars + lo + u) : 0;
-            slot[u] = u < n ? __ldcs(F.vpos + lo + u) : 0;
-            old[u] = u < n ? __ldcs(a2v + lo + u) : 1.f;
+    if (w < F.n_twarps) {  // warp-uniform
+        const int4 wr = __ldg(F.twarps + w);  // {first edge, end edge, first factor, end factor}
+        const int nf = wr.w - wr.z, ne_w = wr.y - wr.x;
+        int fst = 0, ftyp = 0, fgr = -1;
+        float fpar = 0.f;
+        if (lane < nf) {
+            fst = __ldg(g.fptr + wr.z + lane) - wr.x;
+            ftyp = __ldg(g.ftype + wr.z + lane);
+            fpar = __ldg(g.fparam + wr.z + lane);
+            if (F.batch.n_graphs > 0) fgr = __ldg(F.fgraph + wr.z + lane);
         }
-        uint2 bl[K];
-#pragma unroll
-        for (int u = 0; u < K; ++u) bl[u] = u < n ? __ldg(F.belief + v[u]) : make_uint2(0x3f800000u, 0u);
-#pragma unroll
-        for (int u = 0; u < K; ++u)
-            if (u < nw) x[u] = v2a_from_belief(bl[u], old[u]);
-    }
-    const bool eq = type == kTypeEQ, fin = type == kTypeOR, fout = type == kTypeOR || type == kTypeNOT;
-    const int np = eq ? n : n - 1;  // variables in the products: premises (EQ: all)
-    P2 my{1.f, 1.f};
-#pragma unroll
-    for (int u = 0; u < K; ++u)
-        if (u < nw && u == n - 1 && !eq) my = dec(x[u]);
-    if (fin) my = P2{my.m1, my.m0};
-    const bool nz = type == kTypeNOISY_AND || type == kTypePRIOR, ni = type == kTypeNOISY_IMPLY;
-    const float sy = my.m0 + my.m1, w = fmaf(p, my.m1, q * my.m0);
-    // to the output: mu0 = a0 X + D, mu1 = b0 X + b1 D
-    const float a0 = (nz || ni) ? q : 0.f, b0 = (nz || ni) ? p : 1.f, b1 = ni ? 1.f : 0.f;
-    // to a premise: mu0 = c0 Y, mu1 = d0 X + d1 D
-    const float c0 = eq ? 1.f : ni ? sy : my.m0;
-    const float d0 = eq ? 1.f : (nz || ni) ? w : my.m1;
-    const float d1 = eq ? 0.f : ni ? sy : my.m0;
-    auto elem = [&](float r, float &ex, float &ey, float &ed) {
-        P2 m = dec(r);
-        if (fin) m = P2{m.m1, m.m0};
-        ex = m.m1;
-        ed = m.m0;
-        ey = eq ? m.m0 : m.m0 + m.m1;
-    };
-    // prefix runs: pX[u], pY[u], pD[u] over the premises before slot u
-    float pX[K + 1], pY[K + 1], pD[K + 1];
-    pX[0] = 1.f;
-    pY[0] = 1.f;
-    pD[0] = 0.f;
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-        if (u < nw) {
-            float ex, ey, ed;
-            elem(x[u], ex, ey, ed);
-            if (u >= np) ex = ey = 1.f, ed = 0.f;  // the output (or no variable): the identity
-            pX[u + 1] = pX[u] * ex;
-            pY[u + 1] = pY[u] * ey;
-            pD[u + 1] = fmaf(pD[u], ey, pX[u] * ed);
+        const unsigned starts = __reduce_or_sync(0xffffffffu, lane < nf ? 1u << fst : 0u);
+        const unsigned upto = starts & (0xffffffffu >> (31 - lane));  // factor starts at or before this lane
+        const int fi = __popc(upto) - 1;                              // this lane's factor in the warp
+        const int first = 31 - __clz(upto);                           // lane of its first edge
+        const unsigned after = starts & ~(0xffffffffu >> (31 - lane));
+        const bool valid = lane < ne_w;
+        const int n = (after ? __ffs(after) - 1 : ne_w) - first;
+        const int type = __shfl_sync(0xffffffffu, ftyp, fi);
+        const float p = __shfl_sync(0xffffffffu, fpar, fi), q = 1.f - p;
+        const bool eq = type == kTypeEQ, fin = type == kTypeOR, fout = type == kTypeOR || type == kTypeNOT;
+        const int i = lane - first, np = eq ? n : n - 1;
+        const int e = wr.x + lane;
+        float x = 1.f, old = 1.f;
+        int slot = 0;
+        bool frozen = false;
+        if (F.batch.n_graphs > 0) {
+            graph = __shfl_sync(0xffffffffu, fgr, fi);
+            frozen = __ldcg(F.batch.done + graph) != 0;
         }
-    }
-    // suffix run from the last premise down; slot u's message is its prefix
-    // run composed with the suffix run, or (u = np) the output's
-    float sX = 1.f, sY = 1.f, sD = 0.f;
-#pragma unroll
-    for (int u = K - 1; u >= 0; --u) {
-        if (u < nw) {
-            const float X = pX[u] * sX, Y = pY[u] * sY, D = fmaf(pD[u], sY, pX[u] * sD);
-            P2 mu = u == np ? P2{fmaf(a0, X, D), fmaf(b0, X, b1 * D)} : P2{c0 * Y, fmaf(d0, X, d1 * D)};
-            if (fout) mu = P2{mu.m1, mu.m0};
-            if (u < n && (!F.elevel || __ldg(F.elevel + lo + u) == F.level)) {
-                bool gd = false;
-                const float r = enc_fast(mu, gd);
-                ng += gd;
-                const float dd = delta_p1_fast(r, old[u]);
-                dmax = fmaxf(dmax, dd);
-                __stcs(a2v + lo + u, r);
-                a2v_vm[slot[u]] = r;
-                if (F.dres) F.dres[lo + u] = dd;
+        if (valid) {
+            const int v = __ldcs(g.fvars + e);
+            slot = __ldcs(F.vpos + e);
+            old = __ldcs(a2v + e);
+            x = v2a_from_belief(__ldg(F.belief + v), old);
+        } else {
+            graph = -1;
+        }
+        // the output's message (flipped with the inputs for OR)
+        P2 my = dec(__shfl_sync(0xffffffffu, x, (first + n - 1) & 31));
+        if (fin) my = P2{my.m1, my.m0};
+        if (eq) my = P2{1.f, 1.f};
+        float X = 1.f, Y = 1.f, D = 0.f;
+        const int span = __reduce_max_sync(0xffffffffu, valid ? np : 0);
+        for (int j = 0; j < span; ++j) {
+            const float r = __shfl_sync(0xffffffffu, x, (first + j) & 31);
+            if (j < np && j != i) {
+                P2 m = dec(r);
+                if (fin) m = P2{m.m1, m.m0};
+                const float ey = eq ? m.m0 : m.m0 + m.m1;
+                D = fmaf(D, ey, X * m.m0);
+                X *= m.m1;
+                Y *= ey;
             }
-            if (u < np) {
-                float ex, ey, ed;
-                elem(x[u], ex, ey, ed);
-                sD = fmaf(ed, sY, ex * sD);
-                sX *= ex;
-                sY *= ey;
-            }
+        }
+        const bool nz = type == kTypeNOISY_AND || type == kTypePRIOR, ni = type == kTypeNOISY_IMPLY;
+        P2 mu;
+        if (i == np) {  // the output: mu0 = a0 X + D, mu1 = b0 X + b1 D
+            const float a0 = (nz || ni) ? q : 0.f, b0 = (nz || ni) ? p : 1.f, b1 = ni ? 1.f : 0.f;
+            mu = P2{fmaf(a0, X, D), fmaf(b0, X, b1 * D)};
+        } else {        // a premise: mu0 = c0 Y, mu1 = d0 X + d1 D
+            const float sy = my.m0 + my.m1, wq = fmaf(p, my.m1, q * my.m0);
+            const float c0 = eq ? 1.f : ni ? sy : my.m0;
+            const float d0 = eq ? 1.f : (nz || ni) ? wq : my.m1;
+            const float d1 = eq ? 0.f : ni ? sy : my.m0;
+            mu = P2{c0 * Y, fmaf(d0, X, d1 * D)};
+        }
+        if (fout) mu = P2{mu.m1, mu.m0};
+        if (valid && !frozen && (!F.elevel || __ldg(F.elevel + e) == F.level)) {
+            bool gd = false;
+            const float r = enc_fast(mu, gd);
+            ng += gd;
+            dd = delta_p1_fast(r, old);
+            __stcs(a2v + e, r);
+            a2v_vm[slot] = r;
+            if (F.dres) F.dres[e] = dd;
         }
     }
     if (ng) atomicAdd(ctl.guards, ng);
     if (F.batch.n_graphs > 0) {
-        batch_residual(F, graph, dmax);
+        batch_residual(F, graph, dd);
         return;
     }
-    const float bm = block_max(dmax);
+    const float bm = block_max(dd);
     if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
-// Generic factors: one lane per message; each warp holds whole factors (consecutive in the
+// Generic factors: one lane per message; each warp holds whole generic factors (consecutive in the
 // factor-major order, so its edges are one contiguous range and every
 // streamed load and store is coalesced).  The warp reads its factors' row
 // offsets, types and parameters once (lane j: factor j) and each lane finds
@@ -700,9 +676,7 @@ void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a
     const int nb = P.nb_vars + P.nb_medium + (P.n_hub_rows + 7) / 8;
     if (nb > 0) k_beliefs<<<nb, 256, 0, s>>>(g, P, a2v_vm);
     if (P.n_wide > 0) k_wide_v2a<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v);
-    if (g.na > 0) k_a2v_thread<4><<<(g.na + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl, nullptr, g.na);
-    if (P.n_fac8 > 0)
-        k_a2v_thread<8><<<(P.n_fac8 + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl, P.fac8, P.n_fac8);
+    if (P.n_twarps > 0) k_a2v_lanes<<<(P.n_twarps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
     if (P.n_warps > 0) k_a2v_fused<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
     if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
 }
@@ -759,7 +733,7 @@ cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, 
 
 int flood_launches(const DevGraph &g, const FloodPlanDev &F)
 {
-    return (F.n_subs > 0) + (F.nb_vars + F.nb_medium + F.n_hub_rows > 0) + 2 * (F.n_wide > 0) + (g.na > 0) + (F.n_fac8 > 0) +
+    return (F.n_subs > 0) + (F.nb_vars + F.nb_medium + F.n_hub_rows > 0) + 2 * (F.n_wide > 0) + (F.n_twarps > 0) +
            (F.n_warps > 0) + 1;
 }
 

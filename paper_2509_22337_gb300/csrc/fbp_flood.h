@@ -39,13 +39,11 @@ struct FloodPlanDev {
     const int4 *hub_row = nullptr;     // [n_hub_rows] {variable, first agg slot, sub-chunks, 0}
     XP *agg = nullptr;                 // product of each sub-chunk of a row of several
     uint2 *belief = nullptr;           // [nv] belief record of each variable (see fbp_flood.cu)
-    // phase 2 (factor-major): typed factors of at most 4 variables one thread
-    // each, by factor id; typed factors of 5..8 variables one thread each,
-    // from a list; runs of consecutive other factors of at most 32 variables
-    // (generic ones, typed ones of 9..32) in warps of whole factors; factors
-    // wider than a warp edge by edge
-    int32_t n_fac8 = 0;
-    const int32_t *fac8 = nullptr;     // [n_fac8] typed factors of 5..8 variables
+    // phase 2 (factor-major): runs of consecutive typed factors of at most
+    // 32 variables in warps of whole factors (twarps); runs of consecutive
+    // generic factors likewise (warps); factors wider than a warp edge by edge
+    int32_t n_twarps = 0;
+    const int4 *twarps = nullptr;      // [n_twarps] {first edge, end edge, first factor, end factor}
     int32_t n_warps = 0;
     const int4 *warps = nullptr;       // [n_warps] {first edge, end edge, first factor, end factor}
     int32_t n_wide = 0;

@@ -189,7 +189,7 @@ int build_flood_plan(fbp_graph *g)
         dfree(g, (void *)g->flood.agg);
         dfree(g, (void *)g->flood.belief);
         dfree(g, (void *)g->flood.warps);
-        dfree(g, (void *)g->flood.fac8);
+        dfree(g, (void *)g->flood.twarps);
         dfree(g, (void *)g->flood.wide);
         dfree(g, (void *)g->flood.wide_v2a);
         dfree(g, (void *)g->flood.vpos);
@@ -240,46 +240,53 @@ int build_flood_plan(fbp_graph *g)
     F.agg = d_agg;
     F.belief = d_belief;
     F.vpos = d_vpos;
-    // phase 2: typed factors of at most 4 variables are found by id; typed
-    // factors of 5..8 variables are listed; runs of consecutive other factors
-    // of at most 32 variables are packed whole into warps of at most 32
-    // edges; a factor wider than a warp goes edge by edge to the wide list
-    std::vector<int4> warps;
-    std::vector<int32_t> wide, fac8;
+    // phase 2: runs of consecutive typed factors of at most 32 variables are
+    // packed whole into warps of at most 32 edges (twarps), runs of
+    // consecutive generic factors likewise (warps); a factor wider than a
+    // warp goes edge by edge to the wide list
+    std::vector<int4> twarps, warps;
+    std::vector<int32_t> wide;
     {
-        int32_t a0 = 0;  // open warp: first factor
-        auto close = [&](int32_t a1) {
-            if (a1 > a0) warps.push_back(make_int4((int)h.fptr[a0], (int)h.fptr[a1], a0, a1));
-            a0 = a1;
+        int32_t t0 = 0, w0 = 0;  // open typed / generic warp: first factor
+        auto close_t = [&](int32_t a1) {
+            if (a1 > t0) twarps.push_back(make_int4((int)h.fptr[t0], (int)h.fptr[a1], t0, a1));
+            t0 = a1;
+        };
+        auto close_w = [&](int32_t a1) {
+            if (a1 > w0) warps.push_back(make_int4((int)h.fptr[w0], (int)h.fptr[a1], w0, a1));
+            w0 = a1;
         };
         for (int32_t a = 0; a < h.na; ++a) {
             const int64_t n = h.fptr[a + 1] - h.fptr[a];
-            const bool typed = h.ftype[a] != FBP_TERMS;
-            if (typed && n <= 8) {
-                close(a);
-                if (n > 4) fac8.push_back(a);
-                a0 = a + 1;
-                continue;
-            }
             if (n > 32) {
-                close(a);
+                close_t(a);
+                close_w(a);
                 for (int64_t e = h.fptr[a]; e < h.fptr[a + 1]; ++e) wide.push_back((int32_t)e);
-                a0 = a + 1;
+                t0 = w0 = a + 1;
                 continue;
             }
-            if (h.fptr[a + 1] - h.fptr[a0] > 32) close(a);
+            if (h.ftype[a] == FBP_TERMS) {
+                close_t(a);
+                if (h.fptr[a + 1] - h.fptr[w0] > 32) close_w(a);
+                t0 = a + 1;
+            } else {
+                close_w(a);
+                if (h.fptr[a + 1] - h.fptr[t0] > 32) close_t(a);
+                w0 = a + 1;
+            }
         }
-        close(h.na);
+        close_t(h.na);
+        close_w(h.na);
     }
-    int4 *d_warps = nullptr;
-    int32_t *d_wide = nullptr, *d_fac8 = nullptr;
+    int4 *d_warps = nullptr, *d_twarps = nullptr;
+    int32_t *d_wide = nullptr;
     float *d_wide_v2a = nullptr;
-    if ((rc = upload(g, &d_fac8, fac8.data(), fac8.size())) ||
+    if ((rc = upload(g, &d_twarps, twarps.data(), twarps.size())) ||
         (rc = upload(g, &d_warps, warps.data(), warps.size())) || (rc = upload(g, &d_wide, wide.data(), wide.size())) ||
         (rc = dalloc_n(g, &d_wide_v2a, std::max<size_t>(wide.size(), 1))))
         return rc;
-    F.n_fac8 = (int32_t)fac8.size();
-    F.fac8 = d_fac8;
+    F.n_twarps = (int32_t)twarps.size();
+    F.twarps = d_twarps;
     F.n_warps = (int32_t)warps.size();
     F.warps = d_warps;
     F.n_wide = (int32_t)wide.size();

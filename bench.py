@@ -1,17 +1,18 @@
-"""Benchmark: BP message updates/s on the SmartFL-shaped 200k-variable graph.
+"""Benchmark: BP message updates/s on the BINGO-shaped 1M-tuple derivation graph.
 
 One step = one whole run of the hot path on one graph: messages reset to
-uniform, then TOPO_FB sweeps (forward levels then backward levels of the
-dependency analysis) until the largest message change is below 1e-6 or 100
-sweeps, then the marginals (Eq. 3) into a device buffer.  `value` counts the
-factor-to-variable message updates of the step over its device time (CUDA
-events on the library's stream), graph already resident in HBM.  The L2 is
-flushed (a 512 MiB write) between timed steps because the graph (~45 MiB of
-device data) fits in the 126 MiB L2.
+uniform, then flooding (PARALL) iterations until the largest message change
+is below 1e-6 or 500 iterations, then the marginals (Eq. 3) into a device
+buffer.  `value` counts the factor-to-variable message updates of the step
+over its device time (CUDA events on the library's stream), graph already
+resident in HBM.  The L2 is flushed (a 512 MiB write) between timed steps.
 
 `e2e` times the same work through the C ABI from host buffers: graph creation
-(CSR transpose, host-to-device copies), schedule construction (Algorithm 2 on
-the host), the run, and the marginals copied back to the host.
+(CSR transpose, host-to-device copies), schedule construction, the run, and
+the marginals copied back to the host.  `forms` (one GPU only) compares, on
+reduced workloads, the batched form against a per-graph launch loop and the
+served form against a cold-start per-request path on the same arrivals.
+`--workload` selects the other configurations.
 
 `--impl reference` times the FP64 oracle (the CPU baseline) on the host cores.
 `--gpus N` under torchrun runs one independent replica per GPU (a single graph
@@ -196,13 +197,14 @@ def algorithmic_bytes_per_half(g):
 
 
 def algorithmic_bytes_flood(g):
-    """Bytes one flooding iteration must move: phase 1 reads each edge's id in
-    its variable's row (4 B), gathers the a->v message (4 B) and scatters the
-    v->a message (4 B); phase 2 reads the v->a message (4 B) and the old a->v
-    message (4 B) and writes the new one (4 B); plus row offsets and unary
-    potentials (8 B/variable) and row offset, type and parameter (9 B/factor)."""
+    """Bytes one flooding iteration of this layout must move: per edge the
+    variable-major message copy read in phase 1 and scattered in phase 2
+    (4 + 4 B), and in phase 2 the edge's variable, its variable-major slot and
+    its message read and written (4 + 4 + 4 + 4 B); per variable its row
+    offset and unary potential read and its 8-byte belief record written and
+    read once (24 B); per factor its row offset, type and parameter (9 B)."""
     E, V, A = g.n_edges, g.n_vars, g.n_factors
-    return 24 * E + 8 * V + 9 * A
+    return 24 * E + 24 * V + 9 * A
 
 
 def pair_model_bytes_per_pass(g):
@@ -248,52 +250,170 @@ def profiled_traffic(kernel: str, workload: str):
     return None
 
 
+def batched_compare(graphs, sch, mi, tol, stream, steps=1, warmup=1, tune=True):
+    """One batched run of `graphs` (fbp_batch, autotuned) against the per-graph
+    fbp_run loop on the same GPU, both from uniform messages with the graphs
+    resident.  Returns the batch's per-step seconds, the loop's seconds, the
+    tuning, the batch's statistics and whether every member's marginals are
+    the same bit for bit both ways."""
+    import torch
+    from paper_2509_22337_gb300 import autotune, fbp_batch as BB
+    from paper_2509_22337_gb300 import fbp as F
+    B = BB.Batch(graphs, sch, mi, tol, stream=stream)
+    tuning = autotune.tune_batch(B, graphs, sch) if tune else None
+    for _ in range(warmup):
+        B.reset()
+        B.run()
+    torch.cuda.synchronize()
+    times, upd = [], 0
+    for _ in range(steps):
+        B.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.run()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        upd += B.stats()["updates"]
+    st = B.stats()
+    Gs = [F.Graph(g, s, stream=stream) for g, s in zip(graphs, sch)]
+    for G in Gs:
+        G.run(1, 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop_upd = 0
+    for G, m, t in zip(Gs, mi, tol):
+        G.reset()
+        G.run(m, t)
+        loop_upd += G.stats()["updates"]
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    same = all(np.array_equal(B.marginals(i), G.marginals()) for i, G in enumerate(Gs))
+    for G in Gs:
+        G.close()
+    B.close()
+    return {"times": times, "updates": upd, "loop_s": loop_s, "loop_updates": loop_upd, "tuning": tuning,
+            "stats": st, "same_results": bool(same)}
+
+
+def serve_window(srv, sids, window):
+    """Submit each request of `window` whose session is served here at its
+    arrival time (relative to the window's first), wait for all.  Returns the
+    requests' infos (latency from submission, queueing included) and the wall
+    seconds."""
+    base = float(window["t"][0])
+    tickets = []
+    start = time.perf_counter()
+    for r in window:
+        if int(r["session"]) not in sids:
+            continue
+        delay = (float(r["t"]) - base) - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(sids[int(r["session"])], int(r["var"]), int(r["value"])))
+    infos = [srv.wait(t)[0] for t in tickets]
+    return infos, time.perf_counter() - start
+
+
+def cold_window(sessions, window, strategy, max_iters, tol):
+    """The cold-start per-request plain path on the same arrivals: each request,
+    at its arrival time and one at a time (FIFO), builds a new graph with its
+    session's evidence so far, runs from uniform messages and reads the
+    marginals back.  Returns per-request service and latency (arrival to
+    result) in ms, and the wall seconds."""
+    import torch
+    from paper_2509_22337_gb300 import fbp as F, gen
+    evid = [np.array(g.evidence, copy=True) for g in sessions]
+    base = float(window["t"][0])
+    svc, lat = [], []
+    start = time.perf_counter()
+    for r in window:
+        evid[int(r["session"])][int(r["var"])] = int(r["value"])
+        delay = (float(r["t"]) - base) - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        g = sessions[int(r["session"])]
+        gc = gen.FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, g.factor_type, g.factor_param, g.prior_p1,
+                             evid[int(r["session"])].copy(), g.name)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        G = F.Graph(gc, strategy)
+        G.run(max_iters, tol)
+        G.marginals()
+        G.close()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        svc.append((t2 - t1) * 1e3)
+        lat.append((t2 - start - (float(r["t"]) - base)) * 1e3)
+    return np.array(svc), np.array(lat), time.perf_counter() - start
+
+
+def _pct(x):
+    return {"p50": round(float(np.percentile(x, 50)), 3), "p99": round(float(np.percentile(x, 99)), 3)}
+
+
+def forms_compare(args, stream):
+    """Reduced batched and served comparisons for the default bench line (one
+    GPU): the batched form against the per-graph loop on the first
+    --forms-graphs graphs of the batched workload's generator; the served form
+    against the cold-start path on the same --forms-requests arrivals of the
+    serving workload's stream over --forms-sessions sessions."""
+    from paper_2509_22337_gb300 import fbp_serve as SV, gen
+    out = {}
+    graphs = gen.batched_mix(n_graphs=args.forms_graphs, seed=4)
+    sch = ["TOPO_FB" if i % 2 == 0 else "PARALL" for i in range(len(graphs))]
+    mi = [100 if s == "TOPO_FB" else 500 for s in sch]
+    r = batched_compare(graphs, sch, mi, [1e-6] * len(graphs), stream)
+    n = len(graphs)
+    bs = float(np.median(r["times"]))
+    out["batched"] = {
+        "graphs": n, "n_edges": int(sum(g.n_edges for g in graphs)),
+        "batched_graphs_per_s": round(n / bs, 2), "loop_graphs_per_s": round(n / r["loop_s"], 2),
+        "speedup_vs_loop": round(r["loop_s"] / bs, 2), "same_results_bit_for_bit": r["same_results"],
+        "tuning": r["tuning"],
+        "what": "one fbp_batch run (autotuned) vs fbp_run per graph on the same GPU, graphs resident, "
+                "from uniform messages; even graphs SmartFL-shaped TOPO_FB, odd BINGO-shaped PARALL"}
+    _, strategy, max_iters, tol, _ = WORKLOADS["serving"]
+    sessions = gen.serving_sessions(args.forms_sessions)
+    window = gen.request_stream(sessions, 2000.0, 30.0)[: args.forms_requests]
+    srv = SV.Server(hbm_budget_bytes=120 << 30, max_inflight=args.serve_inflight, iters_per_tick=args.serve_tick)
+    sids = {i: srv.open(sessions[i], strategy, max_iters, tol) for i in range(len(sessions))}
+    while srv.stats()["sessions_warming"] > 0:
+        time.sleep(0.01)
+    infos, wall = serve_window(srv, sids, window)
+    srv.close()
+    assert all(i["state"] == SV.FBP_REQ_DONE for i in infos), "a served request failed"
+    lat = np.array([i["latency_ms"] for i in infos])
+    svc, clat, cwall = cold_window(sessions, window, strategy, max_iters, tol)
+    out["serving"] = {
+        "sessions": len(sessions), "requests": len(infos), "offered_rate_req_s": 2000.0,
+        "served_req_per_s": round(len(infos) / wall, 2), "served_latency_ms": _pct(lat),
+        "cold_req_per_s": round(len(window) / cwall, 2), "cold_latency_ms": _pct(clat),
+        "cold_service_ms": _pct(svc),
+        "speedup_vs_cold": round((len(infos) / wall) / (len(window) / cwall), 2),
+        "p99_vs_cold": round(float(np.percentile(clat, 99)) / max(float(np.percentile(lat, 99)), 1e-9), 2),
+        "iters_per_request_mean": round(float(np.mean([i["iters"] for i in infos])), 1),
+        "what": "the same arrivals (Poisson 2000 req/s) replayed through the server (resident sessions, "
+                "warm re-runs, continuous batching) and through the cold-start path (new graph with the "
+                "evidence so far, run from uniform messages, marginals to the host), one request at a time; "
+                "latency from arrival to result, queueing included"}
+    return out
+
+
 def run_batched(args, rank, world, local):
     """The batched workload: one fbp_batch run of 512 graphs vs a per-graph loop."""
     import torch
-    from paper_2509_22337_gb300 import autotune, fbp_batch as BB, gen
-    from paper_2509_22337_gb300 import fbp as F
+    from paper_2509_22337_gb300 import fbp_batch as BB, gen
 
     graphs = gen.batched_mix(n_graphs=args.batch_graphs, seed=4 + 1000 * rank)
     sch = ["TOPO_FB" if i % 2 == 0 else "PARALL" for i in range(len(graphs))]
     mi = [100 if s == "TOPO_FB" else 500 for s in sch]
     tol = [1e-6] * len(graphs)
     stream = torch.cuda.current_stream()
-    B = BB.Batch(graphs, sch, mi, tol, stream=stream)
-    tuning = autotune.tune_batch(B, graphs, sch)
-    for _ in range(args.warmup):
-        B.reset()
-        B.run()
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    times, upd = [], 0
     with Clocks(local) as clk:
-        for i in range(args.steps):
-            B.reset()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            B.run()
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-            upd += B.stats()["updates"]
-    st = B.stats()
-    total = float(sum(times))
-    # the per-graph launch loop on the same GPU (graphs resident, one pass)
-    Gs = [F.Graph(g, s, stream=stream) for g, s in zip(graphs, sch)]
-    for G, m in zip(Gs, mi):
-        G.run(1, 0.0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    loop_upd = 0
-    for G, m in zip(Gs, mi):
-        G.reset()
-        G.run(m, 1e-6)
-        loop_upd += G.stats()["updates"]
-    torch.cuda.synchronize()
-    loop_s = time.perf_counter() - t0
-    for G in Gs:
-        G.close()
+        r = batched_compare(graphs, sch, mi, tol, stream, steps=args.steps, warmup=args.warmup)
+    st, tuning, total = r["stats"], r["tuning"], float(sum(r["times"]))
     # end to end: batch creation from host arrays, run, every marginal to the host
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -308,8 +428,9 @@ def run_batched(args, rank, world, local):
     B2.close()
     h2d = sum(g.nbytes() for g in graphs)
     d2h = sum(4 * g.n_vars for g in graphs)
-    t_max, tot = aggregate(total, upd)
+    t_max, tot = aggregate(total, r["updates"])
     n = len(graphs)
+    loop_s = r["loop_s"]
     if rank == 0:
         line = {
             "metric": "BP message updates/s", "value": round(tot / t_max, 1), "unit": "msg_updates/s",
@@ -321,15 +442,15 @@ def run_batched(args, rank, world, local):
                        "tuning": tuning, "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
             "graphs_per_s": round(n * world * args.steps / t_max, 2),
             "per_graph_loop": {"graphs_per_s": round(n / loop_s, 2), "ms": round(loop_s * 1e3, 2),
-                               "msg_updates_per_s": round(loop_upd / loop_s, 1)},
+                               "msg_updates_per_s": round(r["loop_updates"] / loop_s, 1)},
             "speedup_vs_loop": round((loop_s / n) / (t_max / (n * args.steps * world)), 2),
+            "same_results_bit_for_bit": r["same_results"],
             "max_iters_run": st["iters"],
             "e2e": {"value": round(e2e_upd / e2e_s, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_s * 1e3, 2)},
             "gpu_launches": int(st["kernel_launches"] * args.steps), "clocks": clk.summary(),
         }
         print(json.dumps(line))
-    B.close()
 
 
 class OracleGraph:
@@ -452,9 +573,7 @@ def run_serving(args, rank, world, local):
     stream replayed at its own arrival times, continuous batching by the
     library's server.  One step = one window of the stream (--serve-requests
     arrivals); warm-up windows come from the stream after the timed ones."""
-    import threading
-    import torch
-    from paper_2509_22337_gb300 import fbp as F, fbp_serve as SV, gen
+    from paper_2509_22337_gb300 import fbp_serve as SV, gen
 
     _, strategy, max_iters, tol, desc = WORKLOADS["serving"]
     n_sess = args.serve_sessions
@@ -477,22 +596,10 @@ def run_serving(args, rank, world, local):
     load_s = time.perf_counter() - t0
 
     def replay(window):
-        """Submit each of this rank's requests at its arrival time (relative to
-        the window's first), wait for all; returns (infos, wall seconds)."""
-        base = float(window["t"][0])
-        tickets = []
-        start = time.perf_counter()
-        for r in window:
-            if int(r["session"]) not in sids:
-                continue
-            delay = (float(r["t"]) - base) - (time.perf_counter() - start)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(srv.submit(sids[int(r["session"])], int(r["var"]), int(r["value"])))
-        infos = [srv.wait(t)[0] for t in tickets]
+        infos, dt = serve_window(srv, sids, window)
         for i in infos:
             i["session"] = glob[i["session"]]
-        return infos, time.perf_counter() - start
+        return infos, dt
 
     for w in range(args.warmup):  # warm-up windows: the end of the stream
         replay(stream[len(stream) - per * (w + 1): len(stream) - per * w])
@@ -531,30 +638,9 @@ def run_serving(args, rank, world, local):
     # served form's latency is compared with.
     if rank != 0:
         return
-    cold, cold_lat = [], []
-    evid = [np.array(g.evidence, copy=True) for g in sessions]
     window = stream[: per * args.cold_windows]
-    base = float(window["t"][0])
-    start = time.perf_counter()
-    for r in window:
-        evid[int(r["session"])][int(r["var"])] = int(r["value"])
-        delay = (float(r["t"]) - base) - (time.perf_counter() - start)
-        if delay > 0:
-            time.sleep(delay)
-        g = sessions[int(r["session"])]
-        gc = gen.FactorGraph(g.n_vars, g.factor_ptr, g.factor_vars, g.factor_type, g.factor_param, g.prior_p1,
-                             evid[int(r["session"])].copy(), g.name)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        G = F.Graph(gc, strategy)
-        G.run(max_iters, tol)
-        G.marginals()
-        G.close()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        cold.append((t2 - t1) * 1e3)
-        cold_lat.append((t2 - start - (float(r["t"]) - base)) * 1e3)
-    cold, cold_lat = np.array(cold), np.array(cold_lat)
+    cold, cold_lat, cold_wall = cold_window(sessions, window, strategy, max_iters, tol)
+    cold_rate = len(window) / cold_wall
     n_vars_mean = float(np.mean([sessions[i["session"]].n_vars for i in infos]))
     line = {
         "metric": "served requests/s", "value": round(value, 2), "unit": "req/s", "n_gpus": world,
@@ -572,7 +658,7 @@ def run_serving(args, rank, world, local):
         "device_ms": {"p50": round(float(np.percentile(dev, 50)), 3), "p99": round(float(np.percentile(dev, 99)), 3)},
         "iters_per_request": {"mean": round(float(its.mean()), 1), "max": int(its.max())},
         "load_s": round(load_s, 2),
-        "cold_start": {"req_per_s": round(1e3 / float(cold.mean()), 3),
+        "cold_start": {"req_per_s": round(cold_rate, 3),
                        "service_ms": {"p50": round(float(np.percentile(cold, 50)), 3),
                                       "p99": round(float(np.percentile(cold, 99)), 3)},
                        "latency_ms": {"p50": round(float(np.percentile(cold_lat, 50)), 3),
@@ -581,7 +667,7 @@ def run_serving(args, rank, world, local):
                                  "times",
                        "what": "per request: fbp_graph_create with the evidence so far, fbp_run from uniform "
                                "messages, marginals to the host, destroy; one request at a time, FIFO"},
-        "speedup_vs_cold": round(value / (1e3 / float(cold.mean())), 2),
+        "speedup_vs_cold": round(value / cold_rate, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "flooding iteration kernels of all running requests",
@@ -669,7 +755,7 @@ def run_gpu(args):
         # the unit is one flooding iteration (its five kernels, replayed from
         # a captured CUDA graph): algorithmic bytes per iteration over the
         # device time per iteration
-        kname = "flooding iteration (k_v2a_lean, k_hub_partials, k_v2a_rest, k_a2v_lanes, k_flood_check)"
+        kname = "flooding iteration (k_sub_products, k_beliefs, k_a2v_lanes, k_flood_check)"
         kkey = "flood"
         launches_per_step = max(sweeps, 1)
         bytes_per_launch = pair_model_bytes_per_pass(g)
@@ -733,6 +819,9 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+    forms = None
+    if world == 1 and not args.no_forms:
+        forms = forms_compare(args, stream)
 
     if rank == 0:
         line = {
@@ -746,7 +835,7 @@ def run_gpu(args):
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas{world}"},
             "time_to_converge_ms": round(total_ms / args.steps, 4),
-            "roofline": roof, "level_latency": level_stats, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "level_latency": level_stats, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
@@ -756,27 +845,38 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(workload, budget_s=15.0, impl_line=False):
+def cpu_baseline(workload, budget_s=15.0):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
-    the first few sweeps/iterations of the same graph and schedule."""
+    the first few sweeps/iterations of the same graph and schedule, once on
+    one thread (the paper's single-threaded baseline form) and once with each
+    level's independent updates spread over every host core (same results)."""
     from oracle import oracle as O
     O.build()
     _, strategy, max_iters, tol, _ = WORKLOADS[workload]
     kw, note = ORACLE_SAMPLE_GRAPHS.get(workload, ({}, ""))
     g = make_graph(workload, **kw)
     o = O.Oracle(g)
-    # calibrate: one iteration
+    host = os.cpu_count() or 1
+    # calibrate: one iteration on one thread
     t0 = time.perf_counter()
-    r = o.run(strategy, 1, 0.0)
+    o.run(strategy, 1, 0.0)
     t1 = time.perf_counter() - t0
     iters = int(max(1, min(max_iters, budget_s / max(t1, 1e-6))))
+    unit = "sweeps" if strategy == "TOPO_FB" else "iterations"
+    where = f"{note}, {g.n_edges} edges," if note else f"the full {workload} graph"
     t0 = time.perf_counter()
     r = o.run(strategy, iters, 0.0)
     dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rp = o.run(strategy, iters, 0.0, threads=host)
+    dtp = time.perf_counter() - t0
     return {"value": round(r["updates"] / dt, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {strategy} on "
-                      + (f"{note}, {g.n_edges} edges," if note else f"the full {workload} graph")
-                      + f" from uniform messages ({dt:.1f} s, single thread)"}
+            "host_cores": host,
+            "sample": f"{iters} {unit} of {strategy} on {where} from uniform messages ({dt:.1f} s, single thread)",
+            "parallel": {"value": round(rp["updates"] / dtp, 1), "unit": "msg_updates/s", "cores": rp["threads"],
+                         "kind": "oracle",
+                         "sample": f"the same {iters} {unit}, each level's updates over {rp['threads']} host "
+                                   f"threads ({dtp:.1f} s)"}}
 
 
 def run_reference_alarms(args, world):
@@ -824,14 +924,16 @@ def run_reference(args):
     sample_iters = {"smartfl200k": 4, "bingo1m": 2, "bingo1m_residual": 1, "tiny": 50,
                     "generic200k": 2}[args.workload]
     where = f"{note}, {g.n_edges} edges," if note else "the full graph"
+    host = os.cpu_count() or 1
     for _ in range(args.warmup):
-        o.run(strategy, 1, 0.0)
-    times, upd = [], 0
+        o.run(strategy, 1, 0.0, threads=host)
+    times, upd, used = [], 0, 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = o.run(strategy, sample_iters, 0.0)
+        r = o.run(strategy, sample_iters, 0.0, threads=host)
         times.append(time.perf_counter() - t0)
         upd += r["updates"]
+        used = r["threads"]
     tot = float(sum(times))
     value = upd / tot
     line = {
@@ -840,10 +942,12 @@ def run_reference(args):
         "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "strategy": strategy,
-                   "sample": f"{sample_iters} sweeps of {where} per step",
+                   "sample": f"{sample_iters} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {where} per step",
                    "sample_n_vars": g.n_vars, "sample_n_edges": g.n_edges},
-        "cpu_baseline": {"value": round(value, 1), "unit": "msg_updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample_iters} {strategy} sweeps of {where} per step"},
+        "cpu_baseline": {"value": round(value, 1), "unit": "msg_updates/s", "cores": used, "kind": "oracle",
+                         "host_cores": host,
+                         "sample": f"{sample_iters} {strategy} {'sweeps' if strategy == 'TOPO_FB' else 'iterations'} of {where} per step, each level's "
+                                   f"updates over {used} host threads"},
         "e2e": {"value": round(value, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -856,9 +960,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="smartfl200k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bingo1m", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="single-graph workloads: skip the reduced batched and served comparisons")
+    ap.add_argument("--forms-graphs", type=int, default=128, help="graphs of the reduced batched comparison")
+    ap.add_argument("--forms-sessions", type=int, default=16, help="sessions of the reduced served comparison")
+    ap.add_argument("--forms-requests", type=int, default=64, help="requests of the reduced served comparison")
     ap.add_argument("--batch-graphs", type=int, default=512)
     ap.add_argument("--serve-sessions", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=128)

@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* factor type codes (input format); O_TERMS: a generic factor whose local
  * structure is given explicitly as an indicator array (Sec. 4.3.2) */
@@ -638,9 +641,96 @@ static void note_min(run_ws *ws, const double *m)
     if (m[1] > 0.0 && m[1] < ws->min_pos) ws->min_pos = m[1];
 }
 
+/* Host threads a run may use (orc_set_threads).  With more than one, each
+ * level's phase 1 runs over the level's distinct variables in parallel, and
+ * phase 2 and the store over the level's edges in parallel: every one of
+ * those updates reads only the level-start messages and writes its own
+ * entries, and the residual, guard count and range diagnostic are a max, a
+ * sum and a min, so the results are the same as with one thread.  This is
+ * for timing the oracle on every host core; the arithmetic is unchanged. */
+static int g_threads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    int mx = omp_get_num_procs();
+    g_threads = n < 1 ? 1 : n > mx ? mx : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+static void run_levels(const og_graph *g, double *a2v, int64_t k, const int64_t *level_ptr,
+                       const int32_t *level_edges, run_ws *ws, double *residual, int64_t *guards);
+
+#ifdef _OPENMP
+static void run_levels_threads(const og_graph *g, double *a2v, int64_t k, const int64_t *level_ptr,
+                               const int32_t *level_edges, run_ws *ws, double *residual, int64_t *guards)
+{
+    int64_t maxd = 1;
+    for (int32_t v = 0; v < g->nv; v++)
+        if (g->vptr[v + 1] - g->vptr[v] > maxd) maxd = g->vptr[v + 1] - g->vptr[v];
+    int bmax = 1;
+    for (int32_t a = 0; a < g->na; a++)
+        if (g->fptr[a + 1] - g->fptr[a] > bmax) bmax = (int)(g->fptr[a + 1] - g->fptr[a]);
+    const int T = g_threads;
+    double *scratch = (double *)malloc(sizeof(double) * 4 * (maxd + 2) * T);
+    double *mu = (double *)malloc(sizeof(double) * 2 * (bmax + 1) * T);
+    int32_t *vars = (int32_t *)malloc(sizeof(int32_t) * (g->nv + 1));
+    for (int64_t L = 0; L < k; L++) {
+        int64_t lo = level_ptr[L], hi = level_ptr[L + 1], nvl = 0;
+        ws->stamp++;
+        for (int64_t i = lo; i < hi; i++) {
+            int32_t a = g->efac[level_edges[i]];
+            if (ws->fstamp[a] == ws->stamp) continue;
+            ws->fstamp[a] = ws->stamp;
+            for (int64_t q = g->fptr[a]; q < g->fptr[a + 1]; q++) {
+                int32_t v = g->fvars[q];
+                if (ws->vstamp[v] == ws->stamp) continue;
+                ws->vstamp[v] = ws->stamp;
+                vars[nvl++] = v;
+            }
+        }
+#pragma omp parallel for num_threads(T) schedule(dynamic, 256)
+        for (int64_t j = 0; j < nvl; j++)
+            v2a_row(g, a2v, vars[j], ws->v2a, scratch + 4 * (maxd + 2) * omp_get_thread_num());
+        int64_t gsum = 0;
+#pragma omp parallel for num_threads(T) schedule(dynamic, 1024) reduction(+ : gsum)
+        for (int64_t i = lo; i < hi; i++)
+            gsum += a2v_alg1(g, ws->v2a, level_edges[i], ws->newm + 2 * (i - lo),
+                             mu + 2 * (bmax + 1) * omp_get_thread_num());
+        *guards += gsum;
+        double res = *residual, mp = ws->min_pos;
+#pragma omp parallel for num_threads(T) schedule(static) reduction(max : res) reduction(min : mp)
+        for (int64_t i = lo; i < hi; i++) {
+            int64_t e = level_edges[i];
+            const double *nm = ws->newm + 2 * (i - lo);
+            double d = fabs(nm[1] - a2v[2 * e + 1]);
+            if (d > res) res = d;
+            if (ws->dres) ws->dres[e] = d;
+            if (nm[0] > 0.0 && nm[0] < mp) mp = nm[0];
+            if (nm[1] > 0.0 && nm[1] < mp) mp = nm[1];
+            a2v[2 * e] = nm[0];
+            a2v[2 * e + 1] = nm[1];
+        }
+        *residual = res;
+        ws->min_pos = mp;
+    }
+    free(scratch); free(mu); free(vars);
+}
+#endif
+
 static void run_levels(const og_graph *g, double *a2v, int64_t k, const int64_t *level_ptr,
                        const int32_t *level_edges, run_ws *ws, double *residual, int64_t *guards)
 {
+#ifdef _OPENMP
+    if (g_threads > 1) {
+        run_levels_threads(g, a2v, k, level_ptr, level_edges, ws, residual, guards);
+        return;
+    }
+#endif
     for (int64_t L = 0; L < k; L++) {
         int64_t lo = level_ptr[L], hi = level_ptr[L + 1];
         ws->stamp++;

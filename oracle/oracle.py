@@ -45,8 +45,12 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall",
+            "-Wno-unused-function", "-o", tmp, _SRC, "-lm"]
+    # OpenMP only spreads a level's independent updates over host threads
+    # (orc_set_threads); without it the oracle runs on one thread
+    if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -88,6 +92,8 @@ def lib():
             L.orc_update_edges.restype = C.c_int
             L.orc_residual_classes.argtypes = [C.c_void_p, _f64, C.c_double, _i64, _i64]
             L.orc_residual_classes.restype = C.c_int64
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
             _lib = L
     return _lib
 
@@ -173,7 +179,18 @@ class Oracle:
 
     def run(self, strategy="PARALL", max_iters: int = 50, tol: float = 0.0,
             custom: np.ndarray | None = None, def2: bool = False, a2v: np.ndarray | None = None,
-            history: bool = False) -> dict:
+            history: bool = False, threads: int = 1) -> dict:
+        """threads > 1 runs each level's independent updates on that many host
+        threads (same results; out["threads"] is the count actually used)."""
+        used = lib().orc_set_threads(int(threads))
+        try:
+            out = self._run(strategy, max_iters, tol, custom, def2, a2v, history)
+        finally:
+            lib().orc_set_threads(1)
+        out["threads"] = used
+        return out
+
+    def _run(self, strategy, max_iters, tol, custom, def2, a2v, history) -> dict:
         s = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
         init = a2v is not None
         msgs = (np.ascontiguousarray(a2v, np.float64).reshape(-1).copy() if init

@@ -581,3 +581,18 @@ def test_generic_terms_rejected_when_malformed():
                             g.prior_p1, g.evidence, "bad", {}, terms)
         with pytest.raises(ValueError):
             O.Oracle(h)
+
+
+def test_oracle_threads_give_the_same_results():
+    """The oracle's multi-threaded mode (each level's independent updates on
+    several host threads, used to time it on every core) computes exactly the
+    one-thread run: messages, residual history, guards and range diagnostic."""
+    cases = [(gen.tiny(), "PARALL"), (gen.smartfl(n_layers=12, width=40, seed=5), "TOPO_FB"),
+             (gen.bingo(n_tuples=3000, seed=8), "PARALL"), (gen.bingo(n_tuples=2000, seed=9), "RESIDUAL")]
+    for g, strategy in cases:
+        o = O.Oracle(g)
+        a = o.run(strategy, 8, 0.0, history=True)
+        b = o.run(strategy, 8, 0.0, history=True, threads=4)
+        assert np.array_equal(a["a2v"], b["a2v"]), (g.name, strategy)
+        assert np.array_equal(a["res_hist"], b["res_hist"]) and a["guards"] == b["guards"]
+        assert a["min_pos"] == b["min_pos"] and a["updates"] == b["updates"]

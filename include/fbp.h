@@ -220,13 +220,24 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  *                      Neither split option changes a result: a long row's
  *                      product is grouped in 256-entry sub-chunks whichever
  *                      kernel carries it, so messages are bit-identical.
+ * FBP_OPT_ENGINE_FUSE_LANES  level fusion of the grid engine (0..256,
+ *                      default 0 = off): a level of at most this many lanes
+ *                      (one lane per variable of each factor it touches) and
+ *                      no factor wider than a warp runs in one block, and
+ *                      consecutive such levels of an iteration are separated
+ *                      by block barriers instead of grid barriers.  Levels
+ *                      are never merged: results are unchanged.
+ * FBP_OPT_ENGINE_SOLO_LANES  the whole run goes to one block when the
+ *                      schedule's levels average at most this many lanes
+ *                      (default 128; 0 = never).  Results are unchanged.
  * FBP_OPT_RESIDUAL_DEVICE 1 (default): RESIDUAL builds each iteration's
  *                      classes and Algorithm 2 levels on the device and runs
  *                      the levels with the flooding kernels; 0: classes and
  *                      levels on the host, levels run by the level engine. */
 enum {
     FBP_OPT_SPIN_LIMIT = 1, FBP_OPT_ENGINE_GRID = 2, FBP_OPT_ENGINE = 3, FBP_OPT_ENGINE_CLUSTER = 4,
-    FBP_OPT_FLOOD_HUB_MIN = 5, FBP_OPT_FLOOD_CHUNK = 6, FBP_OPT_RESIDUAL_DEVICE = 7
+    FBP_OPT_FLOOD_HUB_MIN = 5, FBP_OPT_FLOOD_CHUNK = 6, FBP_OPT_RESIDUAL_DEVICE = 7,
+    FBP_OPT_ENGINE_FUSE_LANES = 8, FBP_OPT_ENGINE_SOLO_LANES = 9
 };
 int fbp_set_option(fbp_graph *g, int32_t option, int64_t value);
 

@@ -45,13 +45,18 @@ typedef struct fbp_batch fbp_batch;
 
 /* Launch shapes (the autotuner's knobs): blocks of the level engine (0 =
  * automatic), whether it runs as one thread-block cluster (0 automatic, 1
- * never, 8 or 16 = cluster size), and the flooding split of long variable
- * rows over blocks (FBP_OPT_FLOOD_HUB_MIN / FBP_OPT_FLOOD_CHUNK; 0 = default). */
+ * never, 8 or 16 = cluster size), the flooding split of long variable rows
+ * over blocks (FBP_OPT_FLOOD_HUB_MIN / FBP_OPT_FLOOD_CHUNK; 0 = default), and
+ * the engine's level-fusion and one-block thresholds
+ * (FBP_OPT_ENGINE_FUSE_LANES, FBP_OPT_ENGINE_SOLO_LANES; -1 = default).  No
+ * knob changes a result. */
 typedef struct {
     int32_t engine_grid;
     int32_t engine_cluster;
     int32_t flood_hub_min;
     int32_t flood_chunk;
+    int32_t engine_fuse_lanes;
+    int32_t engine_solo_lanes;
 } fbp_batch_tuning;
 
 /* Build every graph on the device (copies all arrays; Algorithm 2 per graph

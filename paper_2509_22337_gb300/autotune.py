@@ -9,9 +9,13 @@ which the tests check, so the timing-dependent pick never changes a result:
 * static strategies (persistent level engine): grid mode with 1, 1/2 or 2
   blocks per SM, a single block (block barriers between levels: for narrow
   levels), one 16-block cluster, or one launch per level (the paper's
-  execution);
-* flooding: how long a variable row may get before it is split over blocks
-  (the threads-per-message split of long rows) and the split's chunk size.
+  execution); the level-fusion threshold (runs of consecutive levels of at
+  most that many lanes go to one block between grid barriers) and the
+  one-block threshold (the whole run in one block when the levels average at
+  most that many lanes);
+* flooding: how long a variable row may get before its sub-chunk products
+  are combined by a warp instead of one thread, and the block size of the
+  sub-chunk pass (the threads-per-message split of long rows).
 
 Choices are cached in a JSON file keyed by a signature of the graph
 (strategy, size and level-shape buckets), so a second graph of the same shape
@@ -86,11 +90,17 @@ def graph_candidates(strategy: str):
             for chunk in (512, 1024, 2048):
                 yield {F.FBP_OPT_FLOOD_HUB_MIN: hub, F.FBP_OPT_FLOOD_CHUNK: chunk}
         return
-    yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: 0}
+    base = {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: 0,
+            F.FBP_OPT_ENGINE_FUSE_LANES: 0, F.FBP_OPT_ENGINE_SOLO_LANES: 128}
+    yield dict(base)
     for grid in (1, sms // 2, sms, 2 * sms):
-        yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: grid}
-    yield {F.FBP_OPT_ENGINE: 1, F.FBP_OPT_ENGINE_CLUSTER: 16, F.FBP_OPT_ENGINE_GRID: 0}
-    yield {F.FBP_OPT_ENGINE: 0, F.FBP_OPT_ENGINE_CLUSTER: 1, F.FBP_OPT_ENGINE_GRID: 0}
+        yield {**base, F.FBP_OPT_ENGINE_GRID: grid}
+    for solo in (0, 32, 512):
+        yield {**base, F.FBP_OPT_ENGINE_SOLO_LANES: solo}
+    for fuse in (32, 64, 128, 256):  # level fusion inside the grid run (one-block switch off)
+        yield {**base, F.FBP_OPT_ENGINE_FUSE_LANES: fuse, F.FBP_OPT_ENGINE_SOLO_LANES: 0}
+    yield {**base, F.FBP_OPT_ENGINE_CLUSTER: 16}
+    yield {**base, F.FBP_OPT_ENGINE: 0}
 
 
 def _apply(G, opts):
@@ -136,7 +146,11 @@ def batch_candidates():
     for cluster in (1, 16):
         for grid in ((0, sms, 2 * sms) if cluster == 1 else (0,)):
             for hub in (128, 256):
-                yield dict(engine_grid=grid, engine_cluster=cluster, flood_hub_min=hub, flood_chunk=1024)
+                yield dict(engine_grid=grid, engine_cluster=cluster, flood_hub_min=hub, flood_chunk=8192,
+                           engine_fuse_lanes=0, engine_solo_lanes=128)
+    for fuse in (64, 256):
+        yield dict(engine_grid=0, engine_cluster=1, flood_hub_min=256, flood_chunk=8192, engine_fuse_lanes=fuse,
+                   engine_solo_lanes=0)
 
 
 def tune_batch(B, graphs, schedules, use_cache: bool = True) -> dict:

@@ -70,7 +70,7 @@ struct fbp_batch {
     Part parts[kParts];
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr};
-    fbp_batch_tuning tuning{0, 0, 0, 0};
+    fbp_batch_tuning tuning{0, 0, 0, 0, -1, -1};
     fbp_stats stats{};
     float *scratch = nullptr;  // [largest union] marginals / pairs staging
     size_t scratch_n = 0;
@@ -453,10 +453,17 @@ extern "C" int fbp_batch_reset(fbp_batch *b)
 extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
 {
     if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
-    const fbp_batch_tuning v = t ? *t : fbp_batch_tuning{0, 0, 0, 0};
+    const fbp_batch_tuning v = t ? *t : fbp_batch_tuning{0, 0, 0, 0, -1, -1};
     if (v.engine_grid < 0 ||
         (v.engine_cluster != 0 && v.engine_cluster != 1 && v.engine_cluster != 8 && v.engine_cluster != 16))
         return fail(FBP_ERR_INVALID_ARG, "bad tuning");
+    for (int k : {kStatic1, kStatic2}) {
+        Part &S = b->parts[k];
+        if (!S.g) continue;
+        int rc = fbp_set_option(S.g, FBP_OPT_ENGINE_FUSE_LANES, v.engine_fuse_lanes >= 0 ? v.engine_fuse_lanes : 0);
+        if (!rc) rc = fbp_set_option(S.g, FBP_OPT_ENGINE_SOLO_LANES, v.engine_solo_lanes >= 0 ? v.engine_solo_lanes : 128);
+        if (rc) return rc;
+    }
     Part &F = b->parts[kFlood];
     if (F.g) {
         int rc = fbp_set_option(F.g, FBP_OPT_FLOOD_HUB_MIN, v.flood_hub_min ? v.flood_hub_min : kFloodMediumMax);

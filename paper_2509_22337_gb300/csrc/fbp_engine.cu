@@ -404,12 +404,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
     const bool solo = gridDim.x == 1;  // one block: block barriers only
     const bool empty = A.n_halves == 0 ||
                        (A.half[0].n_levels == 0 && (A.n_halves < 2 || A.half[1].n_levels == 0));
+    // Level fusion (grid mode): a level of at most A.fuse_lanes lanes and no
+    // factor wider than a warp is "narrow" and runs in block 0 alone (thread
+    // t takes the level's slot t); consecutive narrow levels within an
+    // iteration are separated by block barriers, and the other blocks meet
+    // block 0 at one grid barrier after the last of them.  Each lane computes
+    // exactly what it computes in a grid-wide level.
+    const bool fusing = !kCluster && !solo && A.fuse_lanes > 0;
+    auto narrow = [&](const LevelPlanDev &Q, int l) {
+        return fusing && __ldg(Q.lane_ptr + l + 1) - __ldg(Q.lane_ptr + l) <= A.fuse_lanes &&
+               __ldg(Q.big_ptr + l + 1) == __ldg(Q.big_ptr + l);
+    };
+    auto first_slot = [&](bool nar, int s0, int s1) {
+        return nar ? (blockIdx.x == 0 ? s0 + (int)threadIdx.x : s1) : s0 + my0;
+    };
     Pre<kPre> pre;
+    bool nar = false;
     if (!empty) {
         int h0 = 0;
         while (plan_at(A, h0).n_levels == 0) ++h0;
         const LevelPlanDev P0 = plan_at(A, h0);
-        prefetch(pre, A, P0, P0.level_base, __ldg(P0.lane_ptr) + my0, __ldg(P0.lane_ptr + 1));
+        nar = narrow(P0, 0);
+        const int s0 = __ldg(P0.lane_ptr), s1 = __ldg(P0.lane_ptr + 1);
+        prefetch(pre, A, P0, P0.level_base, first_slot(nar, s0, s1), s1);
     }
     for (it = 1; it <= A.max_iters && !failed && !empty; ++it) {
         float rmax = 0.f;
@@ -430,10 +447,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                     Pn = plan_at(A, hn);
                     if (Pn.n_levels > 0) break;
                 }
+                const bool last_of_iteration = L + 1 == P.n_levels && h + 1 == A.n_halves;
+                const bool nar_n = narrow(Pn, Ln);
+                // a narrow level followed by a narrow one of the same
+                // iteration: block 0 alone, no grid barrier in between
+                const bool fused = nar && nar_n && !last_of_iteration;
                 PreA next;
-                prefetch_a(next, Pn, __ldg(Pn.lane_ptr + Ln) + my0, __ldg(Pn.lane_ptr + Ln + 1));
+                {
+                    const int n0 = __ldg(Pn.lane_ptr + Ln), n1 = __ldg(Pn.lane_ptr + Ln + 1);
+                    prefetch_a(next, Pn, first_slot(nar_n, n0, n1), n1);
+                }
                 run_lane<kPre, false>(pre, A, P, La, cur, nxt, sm, rmax, ng);
-                for (int slot = s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
+                for (int slot = nar ? s1 : s0 + my0 + nthr; slot < s1; slot += nthr) {  // levels wider than the grid
                     Pre<kPre> more;
                     prefetch(more, A, P, La, slot, s1);
                     run_lane<kPre, false>(more, A, P, La, cur, nxt, sm, rmax, ng);
@@ -458,20 +483,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_engine(EngineArgs A)
                     const float bm = block_max(rmax);
                     if (threadIdx.x == 0 && bm > 0.f) max_bits(A.res + (it - 1), __float_as_uint(bm));
                 }
-                // A one-block grid needs no grid barrier: __syncthreads orders
-                // the block's message stores before the next level's loads.
+                // A one-block grid (or block 0 inside a run of fused narrow
+                // levels) needs no grid barrier: __syncthreads orders the
+                // block's message stores before the next level's loads.
                 if (kCluster) {
                     cluster_arrive();
-                } else if (!solo) {
+                } else if (!solo && !fused) {
                     grid_arrive(A.bar);
                     target += gridDim.x;
                 }
                 // the dependent round uses its loads at once: inside the barrier
                 prefetch_b(pre, next, A, Pn, Ln + Pn.level_base);
+                nar = nar_n;
                 if (kCluster) {
                     cluster_wait();
-                } else if (solo) {
-                    __syncthreads();
+                } else if (solo || fused) {
+                    if (blockIdx.x == 0) __syncthreads();
                 } else if (grid_wait(A.bar, target, A.out + 2, A.spin_limit)) {
                     failed = 1;
                     break;

@@ -60,6 +60,8 @@ struct fbp_graph {
     long long spin_limit = 4000000000LL;
     int engine_grid = 0;              // 0 = automatic
     int engine_cluster = 0;           // 0 = automatic, 1 = never, 8 or 16 = cluster size
+    int engine_fuse = 0;              // level fusion: narrow levels (<= this many lanes) in one block (0: off)
+    int engine_solo = 128;            // whole run in one block when levels average <= this many lanes
     int use_engine = 1;
     // flooding plan
     FloodPlanDev flood;

@@ -756,8 +756,6 @@ LevelPlanDev plan_of(const LevelSet &ls)
 // SM (a level's warps are spread round-robin over the blocks), grown if the
 // widest level needs more lanes.  Cluster mode (one cluster, hardware
 // barrier) only when asked for.
-constexpr int64_t kSoloLanes = 128;
-
 void engine_shape(const fbp_graph *g, int *grid, int *cluster)
 {
     int32_t mx = 32;
@@ -776,16 +774,17 @@ void engine_shape(const fbp_graph *g, int *grid, int *cluster)
             return;
         }
     }
-    // With the barrier engine, levels that average at most kSoloLanes lanes
-    // run in one block, whose level barrier is a block barrier (measured on
-    // GB300: 2.5 us per level against 3.4-3.6 us with a grid barrier at 11-100
-    // edges per level; wider levels are faster spread over the grid).
+    // With the barrier engine, levels that average at most engine_solo lanes
+    // (FBP_OPT_ENGINE_SOLO_LANES, default 128) run in one block, whose level
+    // barrier is a block barrier (measured on GB300: 2.5 us per level against
+    // 3.4-3.6 us with a grid barrier at 11-100 edges per level; wider levels
+    // are faster spread over the grid).
     int64_t lanes = 0, levels = 0;
     for (auto &ls : g->halves) {
         lanes += ls.n_lanes;
         levels += (int64_t)ls.lp.size() - 1;
     }
-    if (g->use_engine == 1 && levels > 0 && lanes <= kSoloLanes * levels) {
+    if (g->use_engine == 1 && levels > 0 && lanes <= (int64_t)g->engine_solo * levels) {
         *grid = 1;
         return;
     }
@@ -808,6 +807,7 @@ EngineArgs engine_args(fbp_graph *g)
     A.spin_limit = g->spin_limit;
     for (auto &ls : g->halves) A.max_lanes = std::max(A.max_lanes, ls.max_lanes);
     A.dataflow = g->use_engine == 2;
+    A.fuse_lanes = std::min(g->engine_fuse, engine_block());
     return A;
 }
 
@@ -1217,6 +1217,15 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         if (value != 0 && value != 1 && value != 8 && value != 16)
             return fail(FBP_ERR_INVALID_ARG, "cluster option must be 0, 1, 8 or 16");
         g->engine_cluster = (int)value;
+        return FBP_OK;
+    case FBP_OPT_ENGINE_FUSE_LANES:
+        if (value < 0 || value > engine_block())
+            return fail(FBP_ERR_INVALID_ARG, "fuse threshold must be in [0, %d]", engine_block());
+        g->engine_fuse = (int)value;
+        return FBP_OK;
+    case FBP_OPT_ENGINE_SOLO_LANES:
+        if (value < 0 || value > (1 << 20)) return fail(FBP_ERR_INVALID_ARG, "one-block threshold must be in [0, 2^20]");
+        g->engine_solo = (int)value;
         return FBP_OK;
     default:
         return fail(FBP_ERR_INVALID_ARG, "unknown option %d", option);

@@ -81,6 +81,7 @@ struct EngineArgs {
     long long spin_limit = 0;          // clock64 cycles one barrier may wait
     int32_t max_lanes = 0;             // widest level of the plans, in lanes (launch shape)
     int32_t dataflow = 0;              // grid mode: per-message waits instead of a barrier per level
+    int32_t fuse_lanes = 0;            // grid mode: levels of at most this many lanes run in block 0 (0: off)
     // batched graphs (n_graphs > 0): every lane record carries its graph in
     // bits 15.. of its packed word; each graph stops on its own residual.
     BatchCtl batch;

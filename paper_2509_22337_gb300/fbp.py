@@ -276,6 +276,7 @@ def fbp_messages_import(g, a2v) -> int:
 
 FBP_OPT_SPIN_LIMIT, FBP_OPT_ENGINE_GRID, FBP_OPT_ENGINE, FBP_OPT_ENGINE_CLUSTER = 1, 2, 3, 4
 FBP_OPT_FLOOD_HUB_MIN, FBP_OPT_FLOOD_CHUNK, FBP_OPT_RESIDUAL_DEVICE = 5, 6, 7
+FBP_OPT_ENGINE_FUSE_LANES, FBP_OPT_ENGINE_SOLO_LANES = 8, 9
 
 
 def fbp_set_option(g, option: int, value: int) -> int:

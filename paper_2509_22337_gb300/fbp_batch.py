@@ -17,7 +17,7 @@ class fbp_graph_desc(C.Structure):
 
 class fbp_batch_tuning(C.Structure):
     _fields_ = [("engine_grid", C.c_int32), ("engine_cluster", C.c_int32), ("flood_hub_min", C.c_int32),
-                ("flood_chunk", C.c_int32)]
+                ("flood_chunk", C.c_int32), ("engine_fuse_lanes", C.c_int32), ("engine_solo_lanes", C.c_int32)]
 
 
 def bind(L) -> None:
@@ -93,8 +93,10 @@ def fbp_batch_reset(b):
     return F._check(F.load().fbp_batch_reset(b))
 
 
-def fbp_batch_set_tuning(b, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0):
-    t = fbp_batch_tuning(int(engine_grid), int(engine_cluster), int(flood_hub_min), int(flood_chunk))
+def fbp_batch_set_tuning(b, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0, engine_fuse_lanes=-1,
+                         engine_solo_lanes=-1):
+    t = fbp_batch_tuning(int(engine_grid), int(engine_cluster), int(flood_hub_min), int(flood_chunk),
+                         int(engine_fuse_lanes), int(engine_solo_lanes))
     return F._check(F.load().fbp_batch_set_tuning(b, C.addressof(t)))
 
 
@@ -129,8 +131,10 @@ class Batch:
     def reset(self):
         return fbp_batch_reset(self.h)
 
-    def tune(self, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0):
-        return fbp_batch_set_tuning(self.h, engine_grid, engine_cluster, flood_hub_min, flood_chunk)
+    def tune(self, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0, engine_fuse_lanes=-1,
+             engine_solo_lanes=-1):
+        return fbp_batch_set_tuning(self.h, engine_grid, engine_cluster, flood_hub_min, flood_chunk,
+                                    engine_fuse_lanes, engine_solo_lanes)
 
     def stats(self):
         return fbp_batch_get_stats(self.h)

@@ -334,6 +334,29 @@ def test_engine_grid_size_does_not_change_results(fbp, grid):
     G.close()
 
 
+@pytest.mark.parametrize("fuse", [32, 64, 128, 256])
+def test_level_fusion_does_not_change_results(fbp, fuse):
+    """Level fusion (runs of consecutive levels of at most `fuse` lanes in one
+    block, grid barriers only around them) computes the grid engine's
+    messages bit for bit: layered graphs whose levels straddle the threshold,
+    TOPO_FB (two halves, runs crossing the half boundary) and SEQFIX (every
+    level narrow), with the one-block switch off so that the grid runs."""
+    cases = [(gen.smartfl(n_layers=30, width=24, seed=63), "TOPO_FB"), (gen.smartfl(n_layers=20, width=90, seed=64), "TOPO_FB"),
+             (gen.tiny(), "SEQFIX"), (gen.hub_and_wide(seed=75), "TOPO_FB")]
+    for g, strat in cases:
+        runs = []
+        for f in (0, fuse):
+            G = fbp.Graph(g, strat)
+            G.set_option(fbp.FBP_OPT_ENGINE_SOLO_LANES, 0)
+            G.set_option(fbp.FBP_OPT_ENGINE_FUSE_LANES, f)
+            st, it, res = G.run(4, 0.0)
+            runs.append((G.messages(), G.marginals(), it, np.float32(res).tobytes()))
+            G.close()
+        a, b = runs
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (g.name, strat, fuse)
+        assert a[2] == b[2] and a[3] == b[3]
+
+
 def test_barrier_timeout_is_reported_and_context_survives(fbp):
     """Failure detection without a GPU fault: a spin limit of 0 makes every
     device-side barrier wait that has to wait at all expire at once; the run

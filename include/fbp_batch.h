@@ -65,6 +65,27 @@ typedef struct {
 int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
                      void *cuda_stream, fbp_batch **out);
 
+/* How a batch runs.  one_launch = 1 (the default when the device can launch
+ * thread-block clusters): the whole batch is one persistent kernel launch,
+ * captured once as a CUDA graph; clusters of blocks take whole members from
+ * a queue (largest first) and run each to its own stopping rule, with
+ * barriers among the blocks of a cluster only.  one_launch = 0: the static
+ * members' levels run in one persistent level-engine launch and the flooding
+ * members in captured flooding iterations, side by side on two streams.
+ * Both compute every member's messages as a single-graph run of it does. */
+typedef struct {
+    int32_t one_launch;
+} fbp_batch_config;
+
+/* fbp_batch_create with a configuration (NULL = defaults).  Returns
+ * FBP_ERR_INVALID_ARG for a bad configuration, FBP_ERR_CUDA when one launch
+ * is asked for on a device that cannot launch the queue kernel. */
+int fbp_batch_create_ex(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
+                        void *cuda_stream, const fbp_batch_config *config, fbp_batch **out);
+
+/* 1 if the batch runs in one launch, 0 if on two streams, -1 for NULL. */
+int fbp_batch_one_launch(const fbp_batch *b);
+
 /* Run every graph from its current messages to its own stopping rule.
  * iters_out / residual_out / status_out: [n_graphs] host arrays or NULL;
  * status FBP_OK (converged) or FBP_NOT_CONVERGED.  Returns FBP_OK when all
@@ -80,7 +101,8 @@ int fbp_batch_messages_export(const fbp_batch *b, int32_t graph, float *a2v);
 /* All messages back to uniform (a cold start for the next run). */
 int fbp_batch_reset(fbp_batch *b);
 
-/* Launch shapes; NULL or zero fields = automatic. */
+/* Launch shapes of the two-stream form; NULL or zero fields = automatic.  In
+ * the one-launch form the fields are kept but unused. */
 int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t);
 
 /* Totals of the last run: updates, guards, run_ms (device time of the whole

@@ -24,7 +24,7 @@ using namespace fbp;
 
 namespace {
 
-enum { kFlood = 0, kStatic1 = 1, kStatic2 = 2, kParts = 3 };
+enum { kFlood = 0, kStatic1 = 1, kStatic2 = 2, kQueue = 3, kParts = 4 };
 
 struct Part {
     fbp_graph *g = nullptr;
@@ -39,6 +39,16 @@ struct Part {
     float *tol = nullptr;
     int32_t *maxit = nullptr;
     int32_t *vgraph = nullptr, *fgraph = nullptr;
+    // the one-launch part (every member): member records and queue state
+    std::vector<MemberDev> mem;        // host copy of the member records
+    MemberDev *d_members = nullptr;
+    int32_t *d_order = nullptr;
+    int32_t *d_qwords = nullptr;       // [2 + 4 * clusters]: queue position, error word, per-cluster words
+    unsigned *d_cbar = nullptr;        // [2 * clusters]: barrier counters, residual words
+    int32_t *d_out = nullptr;          // [3 * members]: iterations, status, residual bits
+    int clusters = 0;
+    bool has_flood = false;
+    cudaGraphExec_t exec = nullptr;    // the captured run
     BatchCtl ctl() const
     {
         BatchCtl c;
@@ -69,7 +79,8 @@ struct fbp_batch {
     std::vector<int32_t> nv, ne;
     Part parts[kParts];
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr, nullptr};
+    bool one_launch = false;
     fbp_batch_tuning tuning{0, 0, 0, 0, -1, -1};
     fbp_stats stats{};
     float *scratch = nullptr;  // [largest union] marginals / pairs staging
@@ -78,13 +89,13 @@ struct fbp_batch {
 
 namespace {
 
-int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_allocator *alloc)
+// One union graph of the part's members: their arrays side by side (variable,
+// factor and edge ids offset per member), fac_graph / var_graph the member of
+// every factor / variable.
+int build_union(Part &P, const fbp_graph_desc *graphs, const fbp_allocator *alloc, std::vector<int32_t> &var_graph)
 {
-    Part &P = b->parts[kind];
-    if (P.members.empty()) return FBP_OK;
-    // union arrays
     std::vector<int64_t> fptr(1, 0);
-    std::vector<int32_t> fvars, fac_graph, var_graph;
+    std::vector<int32_t> fvars, fac_graph;
     std::vector<uint8_t> ftype;
     std::vector<float> fparam, prior;
     std::vector<int8_t> ev;
@@ -116,8 +127,19 @@ int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_a
     int rc = fbp_graph_create(nv, na, fptr.data(), fvars.data(), ftype.data(), fparam.data(), prior.data(),
                               ev.data(), alloc, P.stream, &P.g);
     if (rc) return rc;
+    P.g->fac_graph = std::move(fac_graph);
+    return FBP_OK;
+}
+
+int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_allocator *alloc)
+{
+    Part &P = b->parts[kind];
+    if (P.members.empty()) return FBP_OK;
+    std::vector<int32_t> var_graph;
+    int rc = build_union(P, graphs, alloc, var_graph);
+    if (rc) return rc;
     fbp_graph *g = P.g;
-    g->fac_graph = fac_graph;
+    const std::vector<int32_t> &fac_graph = g->fac_graph;
     const int32_t m = (int32_t)P.members.size();
     // per-member state
     std::vector<float> tol(m);
@@ -174,6 +196,216 @@ int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_a
     for (auto &ls : g->halves)
         if ((rc = upload_levels(g, ls))) return rc;
     if (!g->a2v[1] && (rc = dalloc_n(g, &g->a2v[1], (size_t)g->h.ne))) return rc;
+    return FBP_OK;
+}
+
+// The one-launch part: every member in one union graph.  Flooding members
+// get their own ranges of a flooding plan built member by member; static
+// members' own Algorithm 2 level lists are concatenated per half (forward
+// lists of every static member, backward lists of the TOPO_FB members) and
+// packed once, and each member's plan is its range of levels (the packed
+// (edge, level) pairs stay valid: every edge is in exactly one member's
+// levels).  Members are queued largest first.
+int build_queue_part(fbp_batch *b, const fbp_graph_desc *graphs, const fbp_allocator *alloc)
+{
+    Part &P = b->parts[kQueue];
+    if (P.members.empty()) return FBP_OK;
+    std::vector<int32_t> var_graph;
+    int rc = build_union(P, graphs, alloc, var_graph);
+    if (rc) return rc;
+    fbp_graph *g = P.g;
+    const int32_t m = (int32_t)P.members.size();
+    P.mem.assign(m, MemberDev{});
+    std::vector<int4> ranges;
+    std::vector<int32_t> flood_members;
+    for (int32_t k = 0; k < m; ++k) {
+        const fbp_graph_desc &d = graphs[P.members[k]];
+        MemberDev &M = P.mem[k];
+        const int kind = kind_of(d.schedule.strategy);
+        M.kind = kind == kFlood ? 0 : kind == kStatic2 ? 2 : 1;
+        M.v0 = P.var_off[k];
+        M.v1 = M.v0 + d.n_vars;
+        M.e0 = P.edge_off[k];
+        M.e1 = M.e0 + (int32_t)d.factor_ptr[d.n_factors];
+        M.max_iters = d.max_iters;
+        M.tol = (float)d.tol;
+        if (M.kind == 0) {
+            ranges.push_back(make_int4(M.v0, M.v1, P.fac_off[k], P.fac_off[k] + d.n_factors));
+            flood_members.push_back(k);
+        }
+    }
+    if (!ranges.empty()) {
+        std::vector<MemberDev> sl;
+        if ((rc = build_flood_plan(g, &ranges, &sl))) return rc;
+        for (size_t r = 0; r < ranges.size(); ++r) {
+            MemberDev &M = P.mem[flood_members[r]];
+            M.sub0 = sl[r].sub0, M.sub1 = sl[r].sub1, M.med0 = sl[r].med0, M.med1 = sl[r].med1;
+            M.hub0 = sl[r].hub0, M.hub1 = sl[r].hub1, M.tw0 = sl[r].tw0, M.tw1 = sl[r].tw1;
+            M.wide0 = sl[r].wide0, M.wide1 = sl[r].wide1;
+        }
+        if (!g->a2v_vm && (rc = dalloc_n(g, &g->a2v_vm, (size_t)std::max(g->h.ne, 1)))) return rc;
+        P.has_flood = true;
+    }
+    // static members: their own level lists, concatenated per half
+    std::vector<int64_t> lp[2] = {std::vector<int64_t>(1, 0), std::vector<int64_t>(1, 0)};
+    std::vector<int32_t> le[2];
+    std::vector<int32_t> base[2] = {std::vector<int32_t>(m, 0), std::vector<int32_t>(m, 0)};
+    std::vector<int32_t> count[2] = {std::vector<int32_t>(m, 0), std::vector<int32_t>(m, 0)};
+    bool any_static = false;
+    for (int32_t k = 0; k < m; ++k) {
+        if (P.mem[k].kind == 0) continue;
+        any_static = true;
+        const fbp_graph_desc &d = graphs[P.members[k]];
+        HostCSR h;
+        build_host_csr(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param, h);
+        for (int hf = 0; hf < P.mem[k].kind; ++hf) {
+            std::vector<int64_t> rank, lpk;
+            std::vector<int32_t> lek;
+            rc = build_ranks(h, d.schedule, hf, rank);
+            if (rc) {
+                std::string msg = std::string("batch graph ") + std::to_string(P.members[k]) + ": " + fbp_last_error();
+                return fail(rc, "%s", msg.c_str());
+            }
+            dependency_levels(h, rank.data(), nullptr, h.ne, lpk, lek);
+            base[hf][k] = (int32_t)lp[hf].size() - 1;
+            count[hf][k] = (int32_t)lpk.size() - 1;
+            for (size_t L = 0; L + 1 < lpk.size(); ++L) {
+                for (int64_t i = lpk[L]; i < lpk[L + 1]; ++i) le[hf].push_back(lek[i] + P.edge_off[k]);
+                lp[hf].push_back((int64_t)le[hf].size());
+            }
+        }
+    }
+    if (any_static) {
+        free_levels(g);
+        g->halves.clear();
+        const int nh = lp[1].size() > 1 ? 2 : 1;
+        for (int hf = 0; hf < nh; ++hf) {
+            LevelSet ls;
+            ls.lp = std::move(lp[hf]);
+            ls.le = std::move(le[hf]);
+            g->halves.push_back(std::move(ls));
+        }
+        for (auto &ls : g->halves)
+            if ((rc = upload_levels(g, ls))) return rc;
+        if (!g->a2v[1] && (rc = dalloc_n(g, &g->a2v[1], (size_t)std::max(g->h.ne, 1)))) return rc;
+        for (int32_t k = 0; k < m; ++k) {
+            MemberDev &M = P.mem[k];
+            for (int hf = 0; hf < M.kind; ++hf) {
+                LevelPlanDev pl = plan_of(g->halves[hf]);
+                pl.lane_ptr += base[hf][k];
+                pl.big_ptr += base[hf][k];
+                pl.n_levels = count[hf][k];
+                pl.level_base = base[hf][k];
+                M.half[hf] = pl;
+            }
+        }
+    }
+    // largest work first: edges x iterations, static lanes weighted above flooding edges
+    std::vector<int32_t> order(m);
+    std::vector<double> work(m);
+    for (int32_t k = 0; k < m; ++k) {
+        const MemberDev &M = P.mem[k];
+        work[k] = (double)(M.e1 - M.e0) * std::max(M.max_iters, 1) * (M.kind == 0 ? 1.0 : 3.0 * M.kind);
+        order[k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return work[a] > work[c]; });
+    P.clusters = batch_queue_clusters();
+    if (P.clusters < 1) return fail(FBP_ERR_CUDA, "the batch-queue kernel cannot be launched on this device");
+    if ((rc = upload(g, &P.d_members, P.mem.data(), P.mem.size())) || (rc = upload(g, &P.d_order, order.data(), order.size())) ||
+        (rc = dalloc_n(g, &P.d_qwords, (size_t)(2 + 4 * P.clusters))) ||
+        (rc = dalloc_n(g, &P.d_cbar, (size_t)(2 * P.clusters))) || (rc = dalloc_n(g, &P.d_out, (size_t)(3 * m))))
+        return rc;
+    return FBP_OK;
+}
+
+// Enqueue one whole run of the one-launch part: clear the queue and cluster
+// words and the guard counter, refresh the flooding members' variable-major
+// copy, launch the queue kernel.  Captured once as a CUDA graph, replayed.
+int queue_enqueue(fbp_batch *b, Part &P, cudaStream_t s)
+{
+    fbp_graph *g = P.g;
+    cudaError_t e = cudaMemsetAsync(P.d_qwords, 0, sizeof(int32_t) * (2 + 4 * P.clusters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.d_cbar, 0, sizeof(unsigned) * 2 * P.clusters, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue: %s", cudaGetErrorString(e));
+    if (P.has_flood) flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, s);
+    QueueArgs Q;
+    Q.g = g->d;
+    Q.erow = g->erow;
+    Q.a2v = g->a2v[g->cur];
+    Q.a2v_alt = g->a2v[g->cur ^ 1];
+    Q.a2v_vm = g->a2v_vm;
+    Q.F = g->flood;
+    Q.members = P.d_members;
+    Q.order = P.d_order;
+    Q.n_members = (int32_t)P.members.size();
+    Q.queue = P.d_qwords;
+    Q.err = P.d_qwords + 1;
+    Q.cword = P.d_qwords + 2;
+    Q.cbar = P.d_cbar;
+    Q.cres = P.d_cbar + P.clusters;
+    Q.out_iters = P.d_out;
+    Q.out_status = P.d_out + P.members.size();
+    Q.out_res = reinterpret_cast<unsigned *>(P.d_out + 2 * P.members.size());
+    Q.guards = g->d_guards;
+    Q.spin_limit = g->spin_limit;
+    e = launch_batch_queue(Q, P.clusters, s);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue launch: %s", cudaGetErrorString(e));
+    return FBP_OK;
+}
+
+int run_queue(fbp_batch *b, Part &P)
+{
+    fbp_graph *g = P.g;
+    if (!P.exec) {
+        cudaStream_t cap = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue: %s", cudaGetErrorString(e));
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? queue_enqueue(b, P, cap) : FBP_ERR_CUDA;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && rc == FBP_OK) e = cudaGraphInstantiate(&P.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue capture: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaGraphLaunch(P.exec, g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue: %s", cudaGetErrorString(e));
+    b->stats.kernel_launches += 1 + (P.has_flood ? 1 : 0);
+    return FBP_OK;
+}
+
+int collect_queue(fbp_batch *b, Part &P, int32_t *iters_out, double *residual_out, int32_t *status_out, int *all_ok)
+{
+    const size_t m = P.members.size();
+    std::vector<int32_t> out(3 * m);
+    int32_t err = 0;
+    fbp_graph *g = P.g;
+    unsigned long long guards = 0;
+    cudaError_t e = cudaMemcpyAsync(out.data(), P.d_out, sizeof(int32_t) * 3 * m, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, P.d_qwords + 1, sizeof err, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&guards, g->d_guards, sizeof guards, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch collect: %s", cudaGetErrorString(e));
+    if (err) return fail(FBP_ERR_TIMEOUT, "a device-side barrier wait of the batch queue expired");
+    b->stats.guards += (int64_t)guards;
+    for (size_t k = 0; k < m; ++k) {
+        const int32_t i = P.members[k];
+        const int32_t it = out[k];
+        float r;
+        std::memcpy(&r, &out[2 * m + k], sizeof r);
+        const int st = out[m + k] == 0 ? FBP_OK : FBP_NOT_CONVERGED;
+        if (st != FBP_OK) *all_ok = 0;
+        if (iters_out) iters_out[i] = it;
+        if (residual_out) residual_out[i] = (double)r;
+        if (status_out) status_out[i] = st;
+        const MemberDev &M = P.mem[k];
+        b->stats.updates += (int64_t)it * (M.e1 - M.e0) * (M.kind == 0 ? 1 : M.kind);
+        b->stats.iters = std::max(b->stats.iters, it);
+    }
     return FBP_OK;
 }
 
@@ -298,6 +530,12 @@ int collect(fbp_batch *b, Part &P, int32_t *iters_out, double *residual_out, int
 extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
                                 void *cuda_stream, fbp_batch **out)
 {
+    return fbp_batch_create_ex(n_graphs, graphs, alloc, cuda_stream, nullptr, out);
+}
+
+extern "C" int fbp_batch_create_ex(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
+                                   void *cuda_stream, const fbp_batch_config *config, fbp_batch **out)
+{
     if (!out || n_graphs < 0 || (n_graphs > 0 && !graphs)) return fail(FBP_ERR_INVALID_ARG, "bad argument");
     *out = nullptr;
     for (int32_t i = 0; i < n_graphs; ++i) {
@@ -316,13 +554,16 @@ extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, 
             if (d.factor_type[a] == FBP_TERMS)
                 return fail(FBP_ERR_INVALID_ARG, "batch graph %d: generic (FBP_TERMS) factors are for single graphs", i);
     }
+    if (config && config->one_launch != 0 && config->one_launch != 1)
+        return fail(FBP_ERR_INVALID_ARG, "one_launch must be 0 or 1");
     fbp_batch *b = new fbp_batch();
     b->n = n_graphs;
     b->stream = (cudaStream_t)cuda_stream;
+    b->one_launch = config ? config->one_launch == 1 : batch_queue_clusters() > 0;
     b->part_of.resize(n_graphs);
     b->slot_of.resize(n_graphs);
     for (int32_t i = 0; i < n_graphs; ++i) {
-        const int k = kind_of(graphs[i].schedule.strategy);
+        const int k = b->one_launch ? kQueue : kind_of(graphs[i].schedule.strategy);
         b->part_of[i] = k;
         b->slot_of[i] = (int32_t)b->parts[k].members.size();
         b->parts[k].members.push_back(i);
@@ -342,7 +583,7 @@ extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, 
             if (e != cudaSuccess) rc = fail(FBP_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
             P.own_stream = true;
         }
-        if (!rc) rc = build_part(b, k, graphs, alloc);
+        if (!rc) rc = k == kQueue ? build_queue_part(b, graphs, alloc) : build_part(b, k, graphs, alloc);
     }
     cudaError_t e = cudaSuccess;
     if (!rc) e = cudaEventCreate(&b->ev0);
@@ -376,6 +617,7 @@ extern "C" int fbp_batch_run(fbp_batch *b, int32_t *iters_out, double *residual_
     for (auto &P : b->parts)
         if (P.g && P.stream != b->stream) cudaStreamWaitEvent(P.stream, b->ev0, 0);
     int rc = FBP_OK;
+    if (b->parts[kQueue].g) rc = run_queue(b, b->parts[kQueue]);
     for (int k : {kStatic1, kStatic2})
         if (b->parts[k].g && !rc) rc = launch_static(b, b->parts[k]);
     if (!rc && b->parts[kFlood].g) rc = run_flood(b, b->parts[kFlood]);
@@ -402,8 +644,13 @@ extern "C" int fbp_batch_run(fbp_batch *b, int32_t *iters_out, double *residual_
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
     b->stats.run_ms = ms;
     int all_ok = 1;
-    for (auto &P : b->parts)
-        if (P.g && (rc = collect(b, P, iters_out, residual_out, status_out, &all_ok))) return rc;
+    for (int k = 0; k < kParts; ++k) {
+        Part &P = b->parts[k];
+        if (!P.g) continue;
+        rc = k == kQueue ? collect_queue(b, P, iters_out, residual_out, status_out, &all_ok)
+                         : collect(b, P, iters_out, residual_out, status_out, &all_ok);
+        if (rc) return rc;
+    }
     return all_ok ? FBP_OK : FBP_NOT_CONVERGED;
 }
 
@@ -457,6 +704,8 @@ extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
     if (v.engine_grid < 0 ||
         (v.engine_cluster != 0 && v.engine_cluster != 1 && v.engine_cluster != 8 && v.engine_cluster != 16))
         return fail(FBP_ERR_INVALID_ARG, "bad tuning");
+    b->tuning = v;
+    if (b->one_launch) return FBP_OK;  // one launch: the shape is the queue's clusters (fields unused)
     for (int k : {kStatic1, kStatic2}) {
         Part &S = b->parts[k];
         if (!S.g) continue;
@@ -475,6 +724,8 @@ extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
     return FBP_OK;
 }
 
+extern "C" int fbp_batch_one_launch(const fbp_batch *b) { return b ? (b->one_launch ? 1 : 0) : -1; }
+
 extern "C" int fbp_batch_get_stats(const fbp_batch *b, fbp_stats *out)
 {
     if (!b || !out) return fail(FBP_ERR_INVALID_ARG, "NULL argument");
@@ -486,6 +737,7 @@ extern "C" void fbp_batch_destroy(fbp_batch *b)
 {
     if (!b) return;
     for (auto &P : b->parts) {
+        if (P.exec) cudaGraphExecDestroy(P.exec);
         if (P.g) fbp_graph_destroy(P.g);
         if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
     }

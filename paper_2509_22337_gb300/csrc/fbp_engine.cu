@@ -33,6 +33,7 @@
 //  word and every block leaves at its next barrier.
 // Message buffers change between levels, so they are read and written at L2
 // (ld/st.global.cg); the plan and the graph structure are read-only.
+#include "fbp_flood_dev.cuh"
 #include "fbp_msg.cuh"
 
 #include <algorithm>
@@ -673,6 +674,173 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine_df(EngineArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batch queue: a whole batch in one launch.  Thread-block clusters of
+// kQueueCluster blocks take members from a queue (largest first) and run
+// each to its own stopping rule: a flooding member by the flooding items of
+// fbp_flood_dev.cuh over its own ranges of the union's flooding plan, a
+// static member by the level engine's lanes over its own level lists.  The
+// blocks of a cluster are co-scheduled by the hardware, so a barrier among
+// them cannot wait on a block that is not running; clusters never wait on
+// one another, so the launch needs no co-residency beyond a cluster.  The
+// barrier is the grid barrier's counter scheme on the cluster's own word,
+// every wait bounded by spin_limit (an expiry sets the error word, which
+// every cluster sees at its next barrier).  Data the cluster's blocks write
+// for one another between phases is read with coherent loads.
+// ---------------------------------------------------------------------------
+constexpr int kQueueBlock = 256;
+constexpr int kQueueCluster = 8;
+constexpr int kQueuePre = 4;  // row entries per prefetch step (even: same rescaling points as the engine)
+
+__device__ __forceinline__ unsigned cluster_ctarank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_id_x()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+struct ClusterBar {
+    unsigned *ctr;
+    unsigned target;
+    int *err;
+    long long spin;
+    __device__ __forceinline__ int sync()
+    {
+        grid_arrive(ctr);
+        target += kQueueCluster;
+        return grid_wait(ctr, target, err, spin);
+    }
+};
+
+__global__ void __launch_bounds__(kQueueBlock, 2) k_batch_queue(const QueueArgs Q)
+{
+    __shared__ P2 s_m[kQueueBlock];
+    P2 *sm = s_m + (threadIdx.x & ~31);
+    const int r = (int)cluster_ctarank(), c = (int)cluster_id_x();
+    const int gt = r * kQueueBlock + (int)threadIdx.x, nt = kQueueCluster * kQueueBlock;  // thread in the cluster
+    const int gw = gt >> 5, nwp = nt >> 5;                                              // warp in the cluster
+    EngineArgs A;
+    A.g = Q.g;
+    A.erow = Q.erow;
+    ClusterBar bar{Q.cbar + c, 0u, Q.err, Q.spin_limit};
+    int32_t *word = Q.cword + 4 * c;
+    unsigned long long ng = 0;
+    bool failed = false;
+    for (;;) {
+        if (r == 0 && threadIdx.x == 0) word[0] = atomicAdd(Q.queue, 1);
+        if (bar.sync()) break;
+        const int pos = __ldcg(word);
+        if (pos >= Q.n_members) break;
+        const int m = __ldg(Q.order + pos);
+        const MemberDev &M = Q.members[m];
+        int it, status = 1;
+        unsigned rbits = 0;
+        float *cur = Q.a2v, *nxt = Q.a2v_alt;
+        const int kind = M.kind, max_iters = M.max_iters;
+        const float tol = M.tol;
+        const bool empty_static = kind > 0 && M.half[0].n_levels == 0 && (kind < 2 || M.half[1].n_levels == 0);
+        if (empty_static) {  // as the engine: nothing to update, converged at once
+            it = 1;
+            status = 0;
+        }
+        for (it = 1; !empty_static && it <= max_iters; ++it) {
+            float rmax = 0.f;
+            if (kind == 0) {
+                for (int k = M.sub0 + gt; k < M.sub1; k += nt) fdev::sub_product_item<true>(Q.g, Q.F, Q.a2v_vm, k);
+                if ((failed = bar.sync())) break;
+                for (int v = M.v0 + gt; v < M.v1; v += nt) fdev::belief_var_item<true>(Q.g, Q.F, Q.a2v_vm, v);
+                for (int w = M.med0 + gt; w < M.med1; w += nt) fdev::belief_medium_item<true>(Q.g, Q.F, w);
+                for (int hr = M.hub0 + gw; hr < M.hub1; hr += nwp) fdev::belief_hub_warp<true>(Q.g, Q.F, hr);
+                if ((failed = bar.sync())) break;
+                if (M.wide1 > M.wide0) {
+                    for (int k = M.wide0 + gt; k < M.wide1; k += nt) fdev::wide_v2a_item<true>(Q.g, Q.F, Q.a2v, k);
+                    if ((failed = bar.sync())) break;
+                }
+                for (int w = M.tw0 + gw; w < M.tw1; w += nwp) {
+                    float dd = 0.f;
+                    int graph = -1;
+                    fdev::lanes_warp<true>(Q.g, Q.F, Q.a2v, Q.a2v_vm, w, dd, ng, graph);
+                    rmax = fmaxf(rmax, dd);
+                }
+                for (int k = M.wide0 + gt; k < M.wide1; k += nt) {
+                    float dd = 0.f;
+                    int graph = -1;
+                    fdev::wide_a2v_item<true>(Q.g, Q.F, Q.a2v, Q.a2v_vm, k, dd, ng, graph);
+                    rmax = fmaxf(rmax, dd);
+                }
+            } else {
+                for (int h = 0; h < kind && !failed; ++h) {
+                    const LevelPlanDev P = Q.members[m].half[h];  // from memory: no local copy indexed at run time
+                    for (int L = 0; L < P.n_levels; ++L) {
+                        const int La = L + P.level_base;
+                        const int s0 = __ldg(P.lane_ptr + L), s1 = __ldg(P.lane_ptr + L + 1);
+                        // slots come in whole warps (lane_ptr and the stride are multiples of 32)
+                        for (int slot = s0 + gt; slot < s1; slot += nt) {
+                            Pre<kQueuePre> pre;
+                            prefetch(pre, A, P, La, slot, s1);
+                            run_lane<kQueuePre, false>(pre, A, P, La, cur, nxt, sm, rmax, ng);
+                        }
+                        // factors wider than a warp: one thread per edge
+                        const int b0 = __ldg(P.big_ptr + L), b1 = __ldg(P.big_ptr + L + 1);
+                        for (int b = b0 + gt; b < b1; b += nt) {
+                            const int e = __ldg(P.big + b);
+                            const int a = __ldg(A.g.efac + e);
+                            const int lo = __ldg(A.g.fptr + a), n = __ldg(A.g.fptr + a + 1) - lo;
+                            const P2 mu = a2v_unified(__ldg(A.g.ftype + a), __ldg(A.g.fparam + a), n, e - lo,
+                                                      [&](int j) { return v2a_at<false>(A, P, lo + j, La, cur, nxt); });
+                            bool gd = false;
+                            const float rr = enc_fast(mu, gd);
+                            ng += gd;
+                            rmax = fmaxf(rmax, delta_p1_fast(rr, __ldcg(cur + e)));
+                            __stcg(nxt + e, rr);
+                        }
+                        if ((failed = bar.sync())) break;
+                    }
+                    float *t = cur;
+                    cur = nxt;
+                    nxt = t;
+                }
+                if (failed) break;
+            }
+            // the iteration's residual: warp max, one atomic per warp, read
+            // and cleared by block 0 of the cluster, which decides the stop
+            const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));
+            if ((threadIdx.x & 31) == 0 && bits) max_bits(Q.cres + c, bits);
+            if ((failed = bar.sync())) break;
+            if (r == 0 && threadIdx.x == 0) {
+                const unsigned rb = atomicExch(Q.cres + c, 0u);
+                word[1] = __uint_as_float(rb) < tol ? 1 : it >= max_iters ? 2 : 0;
+                word[2] = (int)rb;
+            }
+            if ((failed = bar.sync())) break;
+            const int stop = __ldcg(word + 1);
+            rbits = (unsigned)__ldcg(word + 2);
+            if (stop) {
+                status = stop == 1 ? 0 : 1;
+                break;
+            }
+        }
+        if (failed) break;
+        if (!empty_static && it > max_iters) it = max_iters;
+        // a static member ends with its messages in the first buffer
+        if (kind > 0 && cur != Q.a2v)
+            for (int e = M.e0 + gt; e < M.e1; e += nt) __stcg(Q.a2v + e, __ldcg(cur + e));
+        if (r == 0 && threadIdx.x == 0) {
+            Q.out_iters[m] = it;
+            Q.out_status[m] = status;
+            Q.out_res[m] = rbits;
+        }
+    }
+    if (ng) atomicAdd(Q.guards, ng);
+}
+
 }  // namespace
 
 int engine_block() { return kBlock; }
@@ -763,6 +931,49 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
                                     : (deep ? (const void *)k_engine<false, kBlock, kPreDeep>
                                             : (const void *)k_engine<false, kBlock, kPreWide>);
     return cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBlock), params, 0, s);
+}
+
+int batch_queue_cluster_size() { return kQueueCluster; }
+
+int batch_queue_clusters()
+{
+    static int clusters = -1;
+    if (clusters >= 0) return clusters;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kQueueCluster * 64);
+    cfg.blockDim = dim3(kQueueBlock);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kQueueCluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_batch_queue, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    clusters = n;
+    return clusters;
+}
+
+cudaError_t launch_batch_queue(const QueueArgs &q, int clusters, cudaStream_t s)
+{
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    QueueArgs args = q;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kQueueCluster * clusters);
+    cfg.blockDim = dim3(kQueueBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kQueueCluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_queue, args);
 }
 
 }  // namespace fbp

@@ -12,6 +12,7 @@ struct XP {
     int e0, e1;
     int z0, z1;
 };
+static_assert(sizeof(XP) == 24 && alignof(XP) == 4, "XP: three 8-byte pairs");
 
 constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread each, in row order
 constexpr int kFloodSub = 32;          // the grouping unit of a longer row's product
@@ -62,6 +63,36 @@ struct FloodPlanDev {
     const int32_t *fgraph = nullptr;
     BatchCtl batch;
 };
+
+// The batch-queue kernel's arguments.  Each thread-block cluster takes the
+// next member from the queue (order[queue++]) and runs it to completion;
+// clusters never wait on one another.
+struct QueueArgs {
+    DevGraph g;                        // the union graph of every member
+    const int4 *erow = nullptr;        // [ne] engine row records (static members)
+    float *a2v = nullptr;              // messages in and out (factor-major)
+    float *a2v_alt = nullptr;          // the static members' second buffer
+    float *a2v_vm = nullptr;           // flooding members' variable-major copy
+    FloodPlanDev F;                    // the union's flooding plan (flooding members' ranges)
+    const MemberDev *members = nullptr;
+    const int32_t *order = nullptr;    // members by descending work
+    int32_t n_members = 0;
+    int32_t *queue = nullptr;          // [1] next position in order (zeroed per run)
+    unsigned *cbar = nullptr;          // [clusters] barrier counter of each cluster (zeroed per run)
+    unsigned *cres = nullptr;          // [clusters] residual word of each cluster's current iteration
+    int32_t *cword = nullptr;          // [clusters * 4] words one block publishes to its cluster
+    int32_t *out_iters = nullptr;      // [n_members]
+    int32_t *out_status = nullptr;     // [n_members] 0 converged, 1 stopped at max_iters
+    unsigned *out_res = nullptr;       // [n_members] residual bits of the last iteration
+    unsigned long long *guards = nullptr;
+    int32_t *err = nullptr;            // [1] set when a barrier wait expired
+    long long spin_limit = 0;
+};
+int batch_queue_cluster_size();
+// Clusters of the batch-queue kernel that can be resident at once (0 if the
+// device cannot launch it).
+int batch_queue_clusters();
+cudaError_t launch_batch_queue(const QueueArgs &q, int clusters, cudaStream_t s);
 
 // The flooding kernels keep two copies of the a->v messages: a2v in the
 // factor-major (edge id) order every other part of the library uses, and

@@ -119,7 +119,8 @@ void free_levels(fbp_graph *g);
 // Upload a level list's engine plan: `packed` when given (pack_levels of the
 // same list), else packed here.
 int upload_levels(fbp_graph *g, LevelSet &ls, const fbp::LevelPack *packed = nullptr);
-int build_flood_plan(fbp_graph *g);
+int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges = nullptr,
+                     std::vector<fbp::MemberDev> *slices = nullptr);
 int ensure_res_cap(fbp_graph *g, int32_t n);
 LevelPlanDev plan_of(const LevelSet &ls);
 void engine_shape(const fbp_graph *g, int *grid, int *cluster);

@@ -175,10 +175,14 @@ int upload_erow(fbp_graph *g)
 }
 
 // Flooding plan: variables by degree class (every row of degree <= 8 one
-// thread, medium rows one warp each, hub rows in chunks), the slot of every
-// edge in the variable-major message copy, and phase 2's warps of whole
-// factors.
-int build_flood_plan(fbp_graph *g)
+// thread, longer rows in sub-chunks combined by one thread or one warp), the
+// slot of every edge in the variable-major message copy, and phase 2's warps
+// of whole factors.  With `ranges` (a batch run in one launch), lists are
+// built only over the given {first variable, end variable, first factor, end
+// factor} ranges, range after range, and each range's slices of the lists are
+// returned in `slices` (one MemberDev per range, flooding fields filled);
+// warps never cross a range boundary.
+int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<MemberDev> *slices)
 {
     const HostCSR &h = g->h;
     flood_exec_drop(g);
@@ -198,20 +202,81 @@ int build_flood_plan(fbp_graph *g)
     }
     FloodPlanDev F;
     std::vector<int4> subs, medium, hub_row;
+    std::vector<int4> twarps, warps;
+    std::vector<int32_t> wide;
     int32_t n_agg = 0;  // sub-chunk products of rows of several sub-chunks
-    for (int32_t v = 0; v < h.nv; ++v) {
-        const int32_t lo = h.vptr[v], hi = h.vptr[v + 1], d = hi - lo;
-        if (d <= kFloodSmallMax) continue;  // the one-thread rows
-        const int32_t ns = (d + kFloodSub - 1) / kFloodSub;
-        for (int32_t c = 0; c < ns; ++c)
-            subs.push_back(make_int4(v, lo + c * kFloodSub, std::min(hi, lo + (c + 1) * kFloodSub), ns == 1 ? -1 : n_agg + c));
-        if (ns == 1) continue;
-        (d <= g->flood_hub_min ? medium : hub_row).push_back(make_int4(v, n_agg, ns, 0));
-        n_agg += ns;
+    std::vector<int4> whole;
+    if (!ranges) whole.push_back(make_int4(0, h.nv, 0, h.na));
+    const std::vector<int4> &R = ranges ? *ranges : whole;
+    if (slices) slices->assign(R.size(), MemberDev{});
+    for (size_t r = 0; r < R.size(); ++r) {
+        const int4 rg = R[r];
+        const size_t sub0 = subs.size(), med0 = medium.size(), hub0 = hub_row.size();
+        for (int32_t v = rg.x; v < rg.y; ++v) {
+            const int32_t lo = h.vptr[v], hi = h.vptr[v + 1], d = hi - lo;
+            if (d <= kFloodSmallMax) continue;  // the one-thread rows
+            const int32_t ns = (d + kFloodSub - 1) / kFloodSub;
+            for (int32_t c = 0; c < ns; ++c)
+                subs.push_back(
+                    make_int4(v, lo + c * kFloodSub, std::min(hi, lo + (c + 1) * kFloodSub), ns == 1 ? -1 : n_agg + c));
+            if (ns == 1) continue;
+            (d <= g->flood_hub_min ? medium : hub_row).push_back(make_int4(v, n_agg, ns, 0));
+            n_agg += ns;
+        }
+        // rows of one sub-chunk count side by side: the combines of a warp then
+        // run the same branches (each row is independent: same results)
+        std::stable_sort(medium.begin() + med0, medium.end(), [](const int4 &a, const int4 &b) { return a.z < b.z; });
+        // phase 2: runs of consecutive typed factors of at most 32 variables
+        // are packed whole into warps of at most 32 edges (twarps), runs of
+        // consecutive generic factors likewise (warps); a factor wider than a
+        // warp goes edge by edge to the wide list
+        const size_t tw0 = twarps.size(), wide0 = wide.size();
+        int32_t t0 = rg.z, w0 = rg.z;  // open typed / generic warp: first factor
+        auto close_t = [&](int32_t a1) {
+            if (a1 > t0) twarps.push_back(make_int4((int)h.fptr[t0], (int)h.fptr[a1], t0, a1));
+            t0 = a1;
+        };
+        auto close_w = [&](int32_t a1) {
+            if (a1 > w0) warps.push_back(make_int4((int)h.fptr[w0], (int)h.fptr[a1], w0, a1));
+            w0 = a1;
+        };
+        for (int32_t a = rg.z; a < rg.w; ++a) {
+            const int64_t n = h.fptr[a + 1] - h.fptr[a];
+            if (n > 32) {
+                close_t(a);
+                close_w(a);
+                for (int64_t e = h.fptr[a]; e < h.fptr[a + 1]; ++e) wide.push_back((int32_t)e);
+                t0 = w0 = a + 1;
+                continue;
+            }
+            if (h.ftype[a] == FBP_TERMS) {
+                close_t(a);
+                if (h.fptr[a + 1] - h.fptr[w0] > 32) close_w(a);
+                t0 = a + 1;
+            } else {
+                close_w(a);
+                if (h.fptr[a + 1] - h.fptr[t0] > 32) close_t(a);
+                w0 = a + 1;
+            }
+        }
+        close_t(rg.w);
+        close_w(rg.w);
+        if (slices) {
+            MemberDev &M = (*slices)[r];
+            M.v0 = rg.x;
+            M.v1 = rg.y;
+            M.sub0 = (int32_t)sub0;
+            M.sub1 = (int32_t)subs.size();
+            M.med0 = (int32_t)med0;
+            M.med1 = (int32_t)medium.size();
+            M.hub0 = (int32_t)hub0;
+            M.hub1 = (int32_t)hub_row.size();
+            M.tw0 = (int32_t)tw0;
+            M.tw1 = (int32_t)twarps.size();
+            M.wide0 = (int32_t)wide0;
+            M.wide1 = (int32_t)wide.size();
+        }
     }
-    // rows of one sub-chunk count side by side: the combines of a warp then
-    // run the same branches (each row is independent: same results)
-    std::stable_sort(medium.begin(), medium.end(), [](const int4 &a, const int4 &b) { return a.z < b.z; });
     // slot of each edge in the variable-major copy: the inverse of vedge
     std::vector<int32_t> vpos(h.ne);
     parallel_for(h.ne, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
@@ -240,44 +305,6 @@ int build_flood_plan(fbp_graph *g)
     F.agg = d_agg;
     F.belief = d_belief;
     F.vpos = d_vpos;
-    // phase 2: runs of consecutive typed factors of at most 32 variables are
-    // packed whole into warps of at most 32 edges (twarps), runs of
-    // consecutive generic factors likewise (warps); a factor wider than a
-    // warp goes edge by edge to the wide list
-    std::vector<int4> twarps, warps;
-    std::vector<int32_t> wide;
-    {
-        int32_t t0 = 0, w0 = 0;  // open typed / generic warp: first factor
-        auto close_t = [&](int32_t a1) {
-            if (a1 > t0) twarps.push_back(make_int4((int)h.fptr[t0], (int)h.fptr[a1], t0, a1));
-            t0 = a1;
-        };
-        auto close_w = [&](int32_t a1) {
-            if (a1 > w0) warps.push_back(make_int4((int)h.fptr[w0], (int)h.fptr[a1], w0, a1));
-            w0 = a1;
-        };
-        for (int32_t a = 0; a < h.na; ++a) {
-            const int64_t n = h.fptr[a + 1] - h.fptr[a];
-            if (n > 32) {
-                close_t(a);
-                close_w(a);
-                for (int64_t e = h.fptr[a]; e < h.fptr[a + 1]; ++e) wide.push_back((int32_t)e);
-                t0 = w0 = a + 1;
-                continue;
-            }
-            if (h.ftype[a] == FBP_TERMS) {
-                close_t(a);
-                if (h.fptr[a + 1] - h.fptr[w0] > 32) close_w(a);
-                t0 = a + 1;
-            } else {
-                close_w(a);
-                if (h.fptr[a + 1] - h.fptr[t0] > 32) close_t(a);
-                w0 = a + 1;
-            }
-        }
-        close_t(h.na);
-        close_w(h.na);
-    }
     int4 *d_warps = nullptr, *d_twarps = nullptr;
     int32_t *d_wide = nullptr;
     float *d_wide_v2a = nullptr;

@@ -95,12 +95,30 @@ int engine_cluster_size();
 // barrier); otherwise a cooperative grid of `grid` blocks.
 cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream_t s);
 
+// One member of a batch run by the batch-queue kernel: a thread-block cluster
+// takes it whole and runs it to its own stopping iteration.
+struct MemberDev {
+    int32_t kind = 0;                  // 0: flooding (PARALL); 1 or 2: level lists per iteration
+    int32_t v0 = 0, v1 = 0;            // variables [v0, v1) of the union graph
+    int32_t e0 = 0, e1 = 0;            // edges [e0, e1)
+    int32_t sub0 = 0, sub1 = 0;        // flooding plan ranges: sub-chunks, medium rows,
+    int32_t med0 = 0, med1 = 0;        //   hub rows, typed-factor warps, wide-list entries
+    int32_t hub0 = 0, hub1 = 0;
+    int32_t tw0 = 0, tw1 = 0;
+    int32_t wide0 = 0, wide1 = 0;
+    int32_t max_iters = 0;
+    float tol = 0.f;
+    LevelPlanDev half[2];              // static members: their own level lists
+};
+
 struct IterCtl {
     unsigned *res = nullptr;           // [kResSlots] residual bits of this iteration
     unsigned long long *guards = nullptr;
 };
 
 int num_sms();
+
+
 
 // Eq. (3).
 void launch_marginals(const DevGraph &g, const float *a2v, float *p1, cudaStream_t s);

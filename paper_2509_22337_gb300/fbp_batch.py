@@ -15,6 +15,10 @@ class fbp_graph_desc(C.Structure):
                 ("max_iters", C.c_int32), ("tol", C.c_double)]
 
 
+class fbp_batch_config(C.Structure):
+    _fields_ = [("one_launch", C.c_int32)]
+
+
 class fbp_batch_tuning(C.Structure):
     _fields_ = [("engine_grid", C.c_int32), ("engine_cluster", C.c_int32), ("flood_hub_min", C.c_int32),
                 ("flood_chunk", C.c_int32), ("engine_fuse_lanes", C.c_int32), ("engine_solo_lanes", C.c_int32)]
@@ -25,6 +29,10 @@ def bind(L) -> None:
     if not hasattr(L, "fbp_batch_create"):
         return
     L.fbp_batch_create.argtypes = [i32, vp, vp, vp, C.POINTER(vp)]
+    L.fbp_batch_create_ex.argtypes = [i32, vp, vp, vp, vp, C.POINTER(vp)]
+    L.fbp_batch_create_ex.restype = C.c_int
+    L.fbp_batch_one_launch.argtypes = [vp]
+    L.fbp_batch_one_launch.restype = C.c_int
     L.fbp_batch_run.argtypes = [vp, vp, vp, vp]
     L.fbp_batch_marginals.argtypes = [vp, i32, vp, C.c_int]
     L.fbp_batch_messages_export.argtypes = [vp, i32, vp]
@@ -40,9 +48,10 @@ def bind(L) -> None:
     S.bind(L)
 
 
-def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=None):
+def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=None, one_launch=None):
     """graphs: list of FactorGraph; schedules: list of strategy names; max_iters,
-    tols: per-graph lists.  Returns (handle, keepalive)."""
+    tols: per-graph lists; one_launch: None (the library's default), True
+    (one persistent launch) or False (two streams).  Returns the handle."""
     L = F.load()
     n = len(graphs)
     descs = (fbp_graph_desc * max(n, 1))()
@@ -61,8 +70,9 @@ def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=N
             F._default_alloc = F.torch_allocator()
         alloc = F._default_alloc
     out = C.c_void_p()
-    F._check(L.fbp_batch_create(n, C.addressof(descs), None if alloc is None else C.addressof(alloc),
-                                F._stream_ptr(stream), C.byref(out)))
+    cfg = None if one_launch is None else fbp_batch_config(1 if one_launch else 0)
+    F._check(L.fbp_batch_create_ex(n, C.addressof(descs), None if alloc is None else C.addressof(alloc),
+                                   F._stream_ptr(stream), None if cfg is None else C.addressof(cfg), C.byref(out)))
     return out.value
 
 
@@ -114,10 +124,11 @@ def fbp_batch_destroy(b):
 class Batch:
     """Owner of one batch handle."""
 
-    def __init__(self, graphs, schedules, max_iters, tols, stream=None):
+    def __init__(self, graphs, schedules, max_iters, tols, stream=None, one_launch=None):
         self.graphs = graphs
         self.n = len(graphs)
-        self.h = fbp_batch_create(graphs, schedules, max_iters, tols, stream=stream)
+        self.h = fbp_batch_create(graphs, schedules, max_iters, tols, stream=stream, one_launch=one_launch)
+        self.one_launch = bool(F.load().fbp_batch_one_launch(self.h))
 
     def run(self):
         return fbp_batch_run(self.h, self.n)

@@ -1,6 +1,8 @@
 """Batched form: many independent graphs in one run must give, for every
 member, exactly what a single-graph run of it gives (same iterations, same
-messages, same marginals), and match the FP64 oracle like a single run."""
+messages, same marginals), and match the FP64 oracle like a single run; in
+both of its forms (one persistent launch of thread-block clusters taking
+members from a queue, and the two-stream form)."""
 import numpy as np
 import pytest
 
@@ -34,16 +36,21 @@ def _mixed_graphs():
     return gs, sch, mi, tol
 
 
-def test_batch_equals_single_runs(fbp):
+@pytest.mark.parametrize("one_launch", [True, False])
+def test_batch_equals_single_runs(fbp, one_launch):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs, sch, mi, tol = _mixed_graphs()
-    bt = B.Batch(gs, sch, mi, tol)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
+    assert bt.one_launch == one_launch
     rc, iters, res, status = bt.run()
+    if one_launch:  # the whole batch: the queue kernel and the refresh of the flooding members' copy
+        assert bt.stats()["kernel_launches"] == 2
     for i, g in enumerate(gs):
         G = fbp.Graph(g, sch[i])
         st, it, r = G.run(mi[i], tol[i])
         assert iters[i] == it, (i, sch[i], iters[i], it)
         assert status[i] == st, i
+        assert np.float32(res[i]).tobytes() == np.float32(r).tobytes(), (i, sch[i], res[i], r)
         assert np.array_equal(bt.messages(i), G.messages()), (i, sch[i])
         assert np.array_equal(bt.marginals(i), G.marginals()), (i, sch[i])
         G.close()
@@ -58,9 +65,9 @@ def test_batch_equals_single_runs(fbp):
 def test_batch_tuning_does_not_change_results(fbp, engine_cluster):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs, sch, mi, tol = _mixed_graphs()
-    ref = B.Batch(gs, sch, mi, tol)
+    ref = B.Batch(gs, sch, mi, tol, one_launch=False)
     ref.run()
-    bt = B.Batch(gs, sch, mi, tol)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=False)
     bt.tune(engine_grid=0, engine_cluster=engine_cluster)
     bt.run()
     for i in range(len(gs)):
@@ -69,13 +76,14 @@ def test_batch_tuning_does_not_change_results(fbp, engine_cluster):
     bt.close()
 
 
-def test_batch_members_match_oracle(fbp):
+@pytest.mark.parametrize("one_launch", [True, False])
+def test_batch_members_match_oracle(fbp, one_launch):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs = [gen.tiny(), gen.smartfl(n_layers=15, width=40, seed=77), gen.bingo(n_tuples=500, seed=78)]
     sch = ["PARALL", "TOPO_FB", "PARALL"]
     mi = [50, 30, 20]
     tol = [0.0, 0.0, 0.0]
-    bt = B.Batch(gs, sch, mi, tol)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
     rc, iters, res, status = bt.run()
     for i, g in enumerate(gs):
         o = O.Oracle(g)
@@ -88,13 +96,14 @@ def test_batch_members_match_oracle(fbp):
     bt.close()
 
 
-def test_batch_single_kind_and_empty_member(fbp):
+@pytest.mark.parametrize("one_launch", [True, False])
+def test_batch_single_kind_and_empty_member(fbp, one_launch):
     from paper_2509_22337_gb300 import fbp_batch as B
     empty = gen.FactorGraph(4, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint8),
                             np.zeros(0, np.float32), np.array([0.2, np.nan, 0.7, np.nan], np.float32),
                             np.full(4, -1, np.int8), "empty")
     gs = [gen.smartfl(n_layers=8, width=30, seed=5), empty, gen.smartfl(n_layers=6, width=20, seed=6)]
-    bt = B.Batch(gs, ["TOPO_FB"] * 3, [20, 20, 20], [1e-6] * 3)
+    bt = B.Batch(gs, ["TOPO_FB"] * 3, [20, 20, 20], [1e-6] * 3, one_launch=one_launch)
     rc, iters, res, status = bt.run()
     np.testing.assert_allclose(bt.marginals(1), [0.2, 0.5, 0.7, 0.5], atol=1e-7)
     assert iters[1] == 1
@@ -115,7 +124,8 @@ def test_many_graphs_of_different_sizes_interleaved(fbp):
     Bh.close()
 
 
-def test_batch_autotuner(fbp, tmp_path, monkeypatch):
+@pytest.mark.parametrize("one_launch", [True, False])
+def test_batch_autotuner(fbp, tmp_path, monkeypatch, one_launch):
     """The batch tuner picks one of its candidates, and the tuned batch
     computes what the untuned one does, bit for bit for every member (no
     launch shape changes the arithmetic); a second call answers from the
@@ -123,9 +133,9 @@ def test_batch_autotuner(fbp, tmp_path, monkeypatch):
     from paper_2509_22337_gb300 import autotune, fbp_batch as B
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     gs, sch, mi, tol = _mixed_graphs()
-    ref = B.Batch(gs, sch, mi, tol)
+    ref = B.Batch(gs, sch, mi, tol, one_launch=False)
     ref.run()
-    bt = B.Batch(gs, sch, mi, tol)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
     best = autotune.tune_batch(bt, gs, sch)
     assert best in list(autotune.batch_candidates())
     bt.reset()

@@ -290,9 +290,29 @@ def batched_compare(graphs, sch, mi, tol, stream, steps=1, warmup=1, tune=True):
     same = all(np.array_equal(B.marginals(i), G.marginals()) for i, G in enumerate(Gs))
     for G in Gs:
         G.close()
+    # the batch's other forms, each timed once after a warm run
+    FORM_ARGS = {"one": dict(one_launch=True), "queue": dict(one_launch=False, static_queue=True),
+                 "engine": dict(one_launch=False, static_queue=False)}
+    others = {}
+    for form, kw in FORM_ARGS.items():
+        if form == B.form:
+            continue
+        B2 = BB.Batch(graphs, sch, mi, tol, stream=stream, **kw)
+        if tune:
+            autotune.tune_batch(B2, graphs, sch)
+        B2.run()
+        B2.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B2.run()
+        torch.cuda.synchronize()
+        others[form] = time.perf_counter() - t0
+        same = same and all(np.array_equal(B.marginals(i), B2.marginals(i)) for i in range(len(graphs)))
+        B2.close()
+    form = B.form
     B.close()
     return {"times": times, "updates": upd, "loop_s": loop_s, "loop_updates": loop_upd, "tuning": tuning,
-            "stats": st, "same_results": bool(same)}
+            "stats": st, "same_results": bool(same), "form": form, "other_forms": others}
 
 
 def serve_window(srv, sids, window):
@@ -369,9 +389,13 @@ def forms_compare(args, stream):
         "graphs": n, "n_edges": int(sum(g.n_edges for g in graphs)),
         "batched_graphs_per_s": round(n / bs, 2), "loop_graphs_per_s": round(n / r["loop_s"], 2),
         "speedup_vs_loop": round(r["loop_s"] / bs, 2), "same_results_bit_for_bit": r["same_results"],
-        "tuning": r["tuning"],
-        "what": "one fbp_batch run (autotuned) vs fbp_run per graph on the same GPU, graphs resident, "
-                "from uniform messages; even graphs SmartFL-shaped TOPO_FB, odd BINGO-shaped PARALL"}
+        "form": r["form"],
+        "other_forms_graphs_per_s": {k: round(n / v, 2) for k, v in r["other_forms"].items()},
+        "what": "one fbp_batch run vs fbp_run per graph on the same GPU, graphs resident, from uniform "
+                "messages; even graphs SmartFL-shaped TOPO_FB, odd BINGO-shaped PARALL; the batch's other forms "
+                "(one: one persistent launch; queue: static members in the member queue beside the flooding "
+                "kernels; engine: static members in the level engine beside them) timed beside it; every "
+                "member's marginals compared bit for bit across all of them"}
     _, strategy, max_iters, tol, _ = WORKLOADS["serving"]
     sessions = gen.serving_sessions(args.forms_sessions)
     window = gen.request_stream(sessions, 2000.0, 30.0)[: args.forms_requests]
@@ -445,6 +469,8 @@ def run_batched(args, rank, world, local):
                                "msg_updates_per_s": round(r["loop_updates"] / loop_s, 1)},
             "speedup_vs_loop": round((loop_s / n) / (t_max / (n * args.steps * world)), 2),
             "same_results_bit_for_bit": r["same_results"],
+            "form": r["form"],
+            "other_forms_graphs_per_s": {k: round(n / v, 2) for k, v in r["other_forms"].items()},
             "max_iters_run": st["iters"],
             "e2e": {"value": round(e2e_upd / e2e_s, 1), "unit": "msg_updates/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_s * 1e3, 2)},

@@ -45,11 +45,15 @@ typedef struct fbp_batch fbp_batch;
 
 /* Launch shapes (the autotuner's knobs): blocks of the level engine (0 =
  * automatic), whether it runs as one thread-block cluster (0 automatic, 1
- * never, 8 or 16 = cluster size), the flooding split of long variable rows
- * over blocks (FBP_OPT_FLOOD_HUB_MIN / FBP_OPT_FLOOD_CHUNK; 0 = default), and
- * the engine's level-fusion and one-block thresholds
- * (FBP_OPT_ENGINE_FUSE_LANES, FBP_OPT_ENGINE_SOLO_LANES; -1 = default).  No
- * knob changes a result. */
+ * never, 8 or 16 = cluster size; for the member queue, 16 = 16-block
+ * clusters, anything else 8), the flooding split of long variable rows over
+ * blocks (FBP_OPT_FLOOD_HUB_MIN / FBP_OPT_FLOOD_CHUNK; 0 = default), the
+ * engine's level-fusion and one-block thresholds (FBP_OPT_ENGINE_FUSE_LANES,
+ * FBP_OPT_ENGINE_SOLO_LANES; -1 = default), and the clusters the member queue
+ * launches (0 = automatic: half of those that can be resident when flooding
+ * members run beside the queue, so that their kernels find free SMs, else
+ * all; larger values are clamped to what can be resident).  No knob changes
+ * a result. */
 typedef struct {
     int32_t engine_grid;
     int32_t engine_cluster;
@@ -57,6 +61,7 @@ typedef struct {
     int32_t flood_chunk;
     int32_t engine_fuse_lanes;
     int32_t engine_solo_lanes;
+    int32_t queue_clusters;
 } fbp_batch_tuning;
 
 /* Build every graph on the device (copies all arrays; Algorithm 2 per graph
@@ -65,16 +70,26 @@ typedef struct {
 int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
                      void *cuda_stream, fbp_batch **out);
 
-/* How a batch runs.  one_launch = 1 (the default when the device can launch
- * thread-block clusters): the whole batch is one persistent kernel launch,
- * captured once as a CUDA graph; clusters of blocks take whole members from
- * a queue (largest first) and run each to its own stopping rule, with
- * barriers among the blocks of a cluster only.  one_launch = 0: the static
- * members' levels run in one persistent level-engine launch and the flooding
- * members in captured flooding iterations, side by side on two streams.
- * Both compute every member's messages as a single-graph run of it does. */
+/* How a batch runs.  Every form computes every member's messages exactly as
+ * a single-graph run of it does.
+ *  - The member queue: one persistent kernel launch (a CUDA graph captured
+ *    once) of thread-block clusters (8 blocks, or 16: fbp_batch_tuning's
+ *    engine_cluster) that take whole members from a queue, largest first,
+ *    and run each to its own stopping rule with barriers among the blocks of
+ *    a cluster only.
+ *  - Flooding side by side: the flooding members together as one union graph
+ *    run by the whole-GPU flooding kernels (captured iterations), on a second
+ *    stream.
+ * one_launch = 1: every member in the member queue (one launch in all).
+ * one_launch = 0, static_queue = 1 (the default): static members in the
+ *   member queue, flooding members side by side; two launches that run
+ *   concurrently (the queue is not a cooperative launch).
+ * one_launch = 0, static_queue = 0: static members in one cooperative level
+ *   engine launch over the union of their levels merged by index, flooding
+ *   members side by side. */
 typedef struct {
     int32_t one_launch;
+    int32_t static_queue;
 } fbp_batch_config;
 
 /* fbp_batch_create with a configuration (NULL = defaults).  Returns
@@ -101,8 +116,10 @@ int fbp_batch_messages_export(const fbp_batch *b, int32_t graph, float *a2v);
 /* All messages back to uniform (a cold start for the next run). */
 int fbp_batch_reset(fbp_batch *b);
 
-/* Launch shapes of the two-stream form; NULL or zero fields = automatic.  In
- * the one-launch form the fields are kept but unused. */
+/* Launch shapes; NULL or zero fields = automatic.  For the member queue,
+ * engine_cluster is its cluster size (16: 16 blocks; otherwise 8) and
+ * engine_grid caps its clusters (0: as many as can be resident; a cap leaves
+ * room for the flooding kernels that run beside it). */
 int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t);
 
 /* Totals of the last run: updates, guards, run_ms (device time of the whole

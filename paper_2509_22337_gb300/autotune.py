@@ -141,34 +141,53 @@ def tune_graph(G, fg, strategy: str, sample_iters: int = 5, use_cache: bool = Tr
     return best
 
 
-def batch_candidates():
+def batch_candidates(form: str = "engine"):
+    """Launch shapes tried for a batch of the given form ("engine": static
+    members in the level engine; "queue": static members in the member queue;
+    "one": every member in the member queue)."""
+    if form == "one":
+        yield from batch_candidates_one()
+        return
     sms = _sms()
+    if form == "queue":
+        # how many member-queue clusters leave room for the flooding kernels
+        # beside them (0: half of the resident ones; a large value: all)
+        for cluster in (8, 16):
+            for qc in (0, sms // 4, 1 << 20):
+                yield dict(engine_grid=0, engine_cluster=cluster, flood_hub_min=256, flood_chunk=8192,
+                           engine_fuse_lanes=0, engine_solo_lanes=128, queue_clusters=qc)
+        yield dict(engine_grid=0, engine_cluster=8, flood_hub_min=128, flood_chunk=8192,
+                   engine_fuse_lanes=0, engine_solo_lanes=128, queue_clusters=0)
+        return
     for cluster in (1, 16):
         for grid in ((0, sms, 2 * sms) if cluster == 1 else (0,)):
             for hub in (128, 256):
                 yield dict(engine_grid=grid, engine_cluster=cluster, flood_hub_min=hub, flood_chunk=8192,
-                           engine_fuse_lanes=0, engine_solo_lanes=128)
+                           engine_fuse_lanes=0, engine_solo_lanes=128, queue_clusters=0)
     for fuse in (64, 256):
         yield dict(engine_grid=0, engine_cluster=1, flood_hub_min=256, flood_chunk=8192, engine_fuse_lanes=fuse,
-                   engine_solo_lanes=0)
+                   engine_solo_lanes=0, queue_clusters=0)
+
+
+def batch_candidates_one():
+    """The one-launch form's knob: blocks per cluster of the member queue."""
+    for cluster in (16, 8):
+        yield dict(engine_grid=0, engine_cluster=cluster, flood_hub_min=256, flood_chunk=8192,
+                   engine_fuse_lanes=0, engine_solo_lanes=128, queue_clusters=0)
 
 
 def tune_batch(B, graphs, schedules, use_cache: bool = True) -> dict:
     """Pick the fastest launch shapes for a fbp_batch.Batch by timing whole
     batch runs from uniform messages; apply and return them."""
-    if getattr(B, "one_launch", False):
-        # one launch: the queue's clusters are the shape; nothing to time
-        best = next(iter(batch_candidates()))
-        B.tune(**best)
-        return best
-    sig = batch_signature(graphs, schedules)
+    form = getattr(B, "form", "one" if getattr(B, "one_launch", False) else "engine")
+    sig = batch_signature(graphs, schedules) + ("" if form == "engine" else "/" + form)
     cache = _load() if use_cache else {}
     if sig in cache:
         best = cache[sig]["tuning"]
         B.tune(**best)
         return best
     results = []
-    for t in batch_candidates():
+    for t in batch_candidates(form):
         B.tune(**t)
         def run():
             B.reset()

@@ -46,7 +46,9 @@ struct Part {
     int32_t *d_qwords = nullptr;       // [2 + 4 * clusters]: queue position, error word, per-cluster words
     unsigned *d_cbar = nullptr;        // [2 * clusters]: barrier counters, residual words
     int32_t *d_out = nullptr;          // [3 * members]: iterations, status, residual bits
-    int clusters = 0;
+    int cluster = 8;                   // blocks per cluster (8 or 16)
+    int clusters = 0;                  // clusters launched (resident at once)
+    int cap8 = 0;                      // clusters the queue words are sized for (the 8-block count)
     bool has_flood = false;
     cudaGraphExec_t exec = nullptr;    // the captured run
     BatchCtl ctl() const
@@ -81,7 +83,7 @@ struct fbp_batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp[kParts] = {nullptr, nullptr, nullptr, nullptr};
     bool one_launch = false;
-    fbp_batch_tuning tuning{0, 0, 0, 0, -1, -1};
+    fbp_batch_tuning tuning{0, 0, 0, 0, -1, -1, 0};
     fbp_stats stats{};
     float *scratch = nullptr;  // [largest union] marginals / pairs staging
     size_t scratch_n = 0;
@@ -309,11 +311,13 @@ int build_queue_part(fbp_batch *b, const fbp_graph_desc *graphs, const fbp_alloc
         order[k] = k;
     }
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return work[a] > work[c]; });
-    P.clusters = batch_queue_clusters();
+    P.cap8 = std::max(batch_queue_clusters(8), batch_queue_clusters(16));
+    P.cluster = 8;
+    P.clusters = batch_queue_clusters(P.cluster);
     if (P.clusters < 1) return fail(FBP_ERR_CUDA, "the batch-queue kernel cannot be launched on this device");
     if ((rc = upload(g, &P.d_members, P.mem.data(), P.mem.size())) || (rc = upload(g, &P.d_order, order.data(), order.size())) ||
-        (rc = dalloc_n(g, &P.d_qwords, (size_t)(2 + 4 * P.clusters))) ||
-        (rc = dalloc_n(g, &P.d_cbar, (size_t)(2 * P.clusters))) || (rc = dalloc_n(g, &P.d_out, (size_t)(3 * m))))
+        (rc = dalloc_n(g, &P.d_qwords, (size_t)(2 + 4 * P.cap8))) ||
+        (rc = dalloc_n(g, &P.d_cbar, (size_t)(2 * P.cap8))) || (rc = dalloc_n(g, &P.d_out, (size_t)(3 * m))))
         return rc;
     return FBP_OK;
 }
@@ -324,8 +328,8 @@ int build_queue_part(fbp_batch *b, const fbp_graph_desc *graphs, const fbp_alloc
 int queue_enqueue(fbp_batch *b, Part &P, cudaStream_t s)
 {
     fbp_graph *g = P.g;
-    cudaError_t e = cudaMemsetAsync(P.d_qwords, 0, sizeof(int32_t) * (2 + 4 * P.clusters), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.d_cbar, 0, sizeof(unsigned) * 2 * P.clusters, s);
+    cudaError_t e = cudaMemsetAsync(P.d_qwords, 0, sizeof(int32_t) * (2 + 4 * P.cap8), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.d_cbar, 0, sizeof(unsigned) * 2 * P.cap8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_guards, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue: %s", cudaGetErrorString(e));
     if (P.has_flood) flood_sync(g->d, g->a2v[g->cur], g->a2v_vm, s);
@@ -343,13 +347,13 @@ int queue_enqueue(fbp_batch *b, Part &P, cudaStream_t s)
     Q.err = P.d_qwords + 1;
     Q.cword = P.d_qwords + 2;
     Q.cbar = P.d_cbar;
-    Q.cres = P.d_cbar + P.clusters;
+    Q.cres = P.d_cbar + P.cap8;
     Q.out_iters = P.d_out;
     Q.out_status = P.d_out + P.members.size();
     Q.out_res = reinterpret_cast<unsigned *>(P.d_out + 2 * P.members.size());
     Q.guards = g->d_guards;
     Q.spin_limit = g->spin_limit;
-    e = launch_batch_queue(Q, P.clusters, s);
+    e = launch_batch_queue(Q, P.cluster, P.clusters, s);
     if (e != cudaSuccess) return fail(FBP_ERR_CUDA, "batch queue launch: %s", cudaGetErrorString(e));
     return FBP_OK;
 }
@@ -525,6 +529,26 @@ int collect(fbp_batch *b, Part &P, int32_t *iters_out, double *residual_out, int
     return FBP_OK;
 }
 
+// The member queue's launch shape: cluster size (16 on request, else 8) and
+// clusters (requested, clamped to what can be resident; 0 = half of that
+// when flooding members run beside the queue on the whole GPU, else all).
+void queue_shape(fbp_batch *b, int cluster, int clusters)
+{
+    Part &Qp = b->parts[kQueue];
+    if (!Qp.g) return;
+    const int want = cluster == 16 ? 16 : 8;
+    const int cl = batch_queue_clusters(want) > 0 ? want : 8;
+    const int fit = batch_queue_clusters(cl);
+    const bool beside = b->parts[kFlood].g != nullptr;
+    const int n = clusters > 0 ? std::min(clusters, fit) : beside ? std::max(1, (fit + 1) / 2) : fit;
+    if (cl != Qp.cluster || n != Qp.clusters) {
+        Qp.cluster = cl;
+        Qp.clusters = n;
+        if (Qp.exec) cudaGraphExecDestroy(Qp.exec);
+        Qp.exec = nullptr;
+    }
+}
+
 }  // namespace
 
 extern "C" int fbp_batch_create(int32_t n_graphs, const fbp_graph_desc *graphs, const fbp_allocator *alloc,
@@ -554,16 +578,20 @@ extern "C" int fbp_batch_create_ex(int32_t n_graphs, const fbp_graph_desc *graph
             if (d.factor_type[a] == FBP_TERMS)
                 return fail(FBP_ERR_INVALID_ARG, "batch graph %d: generic (FBP_TERMS) factors are for single graphs", i);
     }
-    if (config && config->one_launch != 0 && config->one_launch != 1)
-        return fail(FBP_ERR_INVALID_ARG, "one_launch must be 0 or 1");
+    if (config && ((config->one_launch != 0 && config->one_launch != 1) ||
+                   (config->static_queue != 0 && config->static_queue != 1)))
+        return fail(FBP_ERR_INVALID_ARG, "one_launch and static_queue must be 0 or 1");
     fbp_batch *b = new fbp_batch();
     b->n = n_graphs;
     b->stream = (cudaStream_t)cuda_stream;
-    b->one_launch = config ? config->one_launch == 1 : batch_queue_clusters() > 0;
+    const bool can_queue = batch_queue_clusters(8) > 0;
+    b->one_launch = config ? config->one_launch == 1 : false;
+    const bool static_queue = !b->one_launch && (config ? config->static_queue == 1 : can_queue);
     b->part_of.resize(n_graphs);
     b->slot_of.resize(n_graphs);
     for (int32_t i = 0; i < n_graphs; ++i) {
-        const int k = b->one_launch ? kQueue : kind_of(graphs[i].schedule.strategy);
+        const int kind = kind_of(graphs[i].schedule.strategy);
+        const int k = b->one_launch ? kQueue : (static_queue && kind != kFlood) ? kQueue : kind;
         b->part_of[i] = k;
         b->slot_of[i] = (int32_t)b->parts[k].members.size();
         b->parts[k].members.push_back(i);
@@ -586,6 +614,7 @@ extern "C" int fbp_batch_create_ex(int32_t n_graphs, const fbp_graph_desc *graph
         if (!rc) rc = k == kQueue ? build_queue_part(b, graphs, alloc) : build_part(b, k, graphs, alloc);
     }
     cudaError_t e = cudaSuccess;
+    if (!rc) queue_shape(b, 0, 0);
     if (!rc) e = cudaEventCreate(&b->ev0);
     if (!rc && e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     for (int k = 0; k < kParts && !rc && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->evp[k], cudaEventDisableTiming);
@@ -700,12 +729,13 @@ extern "C" int fbp_batch_reset(fbp_batch *b)
 extern "C" int fbp_batch_set_tuning(fbp_batch *b, const fbp_batch_tuning *t)
 {
     if (!b) return fail(FBP_ERR_INVALID_ARG, "NULL batch");
-    const fbp_batch_tuning v = t ? *t : fbp_batch_tuning{0, 0, 0, 0, -1, -1};
-    if (v.engine_grid < 0 ||
+    const fbp_batch_tuning v = t ? *t : fbp_batch_tuning{0, 0, 0, 0, -1, -1, 0};
+    if (v.engine_grid < 0 || v.queue_clusters < 0 ||
         (v.engine_cluster != 0 && v.engine_cluster != 1 && v.engine_cluster != 8 && v.engine_cluster != 16))
         return fail(FBP_ERR_INVALID_ARG, "bad tuning");
     b->tuning = v;
-    if (b->one_launch) return FBP_OK;  // one launch: the shape is the queue's clusters (fields unused)
+    queue_shape(b, v.engine_cluster, v.queue_clusters);
+    if (b->one_launch) return FBP_OK;
     for (int k : {kStatic1, kStatic2}) {
         Part &S = b->parts[k];
         if (!S.g) continue;

@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine_df(EngineArgs A)
 
 // ---------------------------------------------------------------------------
 // Batch queue: a whole batch in one launch.  Thread-block clusters of
-// kQueueCluster blocks take members from a queue (largest first) and run
+// kCl (8 or 16) blocks take members from a queue (largest first) and run
 // each to its own stopping rule: a flooding member by the flooding items of
 // fbp_flood_dev.cuh over its own ranges of the union's flooding plan, a
 // static member by the level engine's lanes over its own level lists.  The
@@ -689,7 +689,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_engine_df(EngineArgs A)
 // for one another between phases is read with coherent loads.
 // ---------------------------------------------------------------------------
 constexpr int kQueueBlock = 256;
-constexpr int kQueueCluster = 8;
 constexpr int kQueuePre = 4;  // row entries per prefetch step (even: same rescaling points as the engine)
 
 __device__ __forceinline__ unsigned cluster_ctarank()
@@ -706,6 +705,7 @@ __device__ __forceinline__ unsigned cluster_id_x()
     return r;
 }
 
+template <int kCl>
 struct ClusterBar {
     unsigned *ctr;
     unsigned target;
@@ -714,22 +714,23 @@ struct ClusterBar {
     __device__ __forceinline__ int sync()
     {
         grid_arrive(ctr);
-        target += kQueueCluster;
+        target += kCl;
         return grid_wait(ctr, target, err, spin);
     }
 };
 
-__global__ void __launch_bounds__(kQueueBlock, 2) k_batch_queue(const QueueArgs Q)
+template <int kCl>
+__global__ void __launch_bounds__(kQueueBlock, 3) k_batch_queue(const QueueArgs Q)
 {
     __shared__ P2 s_m[kQueueBlock];
     P2 *sm = s_m + (threadIdx.x & ~31);
     const int r = (int)cluster_ctarank(), c = (int)cluster_id_x();
-    const int gt = r * kQueueBlock + (int)threadIdx.x, nt = kQueueCluster * kQueueBlock;  // thread in the cluster
+    const int gt = r * kQueueBlock + (int)threadIdx.x, nt = kCl * kQueueBlock;  // thread in the cluster
     const int gw = gt >> 5, nwp = nt >> 5;                                              // warp in the cluster
     EngineArgs A;
     A.g = Q.g;
     A.erow = Q.erow;
-    ClusterBar bar{Q.cbar + c, 0u, Q.err, Q.spin_limit};
+    ClusterBar<kCl> bar{Q.cbar + c, 0u, Q.err, Q.spin_limit};
     int32_t *word = Q.cword + 4 * c;
     unsigned long long ng = 0;
     bool failed = false;
@@ -933,47 +934,59 @@ cudaError_t launch_engine(const EngineArgs &a, int grid, int cluster, cudaStream
     return cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBlock), params, 0, s);
 }
 
-int batch_queue_cluster_size() { return kQueueCluster; }
+namespace {
 
-int batch_queue_clusters()
+const void *queue_kernel(int cluster)
 {
-    static int clusters = -1;
-    if (clusters >= 0) return clusters;
+    return cluster == 16 ? (const void *)k_batch_queue<16> : (const void *)k_batch_queue<8>;
+}
+
+cudaLaunchConfig_t queue_config(int cluster, int clusters, cudaStream_t s, cudaLaunchAttribute *attr)
+{
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kQueueCluster * 64);
+    cfg.gridDim = dim3(cluster * clusters);
     cfg.blockDim = dim3(kQueueBlock);
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = kQueueCluster;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
+    cfg.stream = s;
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = cluster;
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_batch_queue, &cfg) != cudaSuccess) {
+    return cfg;
+}
+
+}  // namespace
+
+int batch_queue_clusters(int cluster)
+{
+    static int clusters[2] = {-1, -1};
+    if (cluster != 8 && cluster != 16) return 0;
+    int &n = clusters[cluster == 16];
+    if (n >= 0) return n;
+    n = 0;
+    if (cluster == 16 &&
+        cudaFuncSetAttribute(queue_kernel(16), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return n;
+    }
+    cudaLaunchAttribute attr;
+    const cudaLaunchConfig_t cfg = queue_config(cluster, 64, nullptr, &attr);
+    if (cudaOccupancyMaxActiveClusters(&n, queue_kernel(cluster), &cfg) != cudaSuccess) {
         cudaGetLastError();
         n = 0;
     }
-    clusters = n;
-    return clusters;
+    return n;
 }
 
-cudaError_t launch_batch_queue(const QueueArgs &q, int clusters, cudaStream_t s)
+cudaError_t launch_batch_queue(const QueueArgs &q, int cluster, int clusters, cudaStream_t s)
 {
-    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    if (clusters < 1 || (cluster != 8 && cluster != 16)) return cudaErrorInvalidConfiguration;
     QueueArgs args = q;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kQueueCluster * clusters);
-    cfg.blockDim = dim3(kQueueBlock);
-    cfg.stream = s;
     cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = kQueueCluster;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_queue, args);
+    const cudaLaunchConfig_t cfg = queue_config(cluster, clusters, s, &attr);
+    return cluster == 16 ? cudaLaunchKernelEx(&cfg, k_batch_queue<16>, args)
+                         : cudaLaunchKernelEx(&cfg, k_batch_queue<8>, args);
 }
 
 }  // namespace fbp

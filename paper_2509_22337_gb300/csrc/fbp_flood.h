@@ -88,11 +88,10 @@ struct QueueArgs {
     int32_t *err = nullptr;            // [1] set when a barrier wait expired
     long long spin_limit = 0;
 };
-int batch_queue_cluster_size();
-// Clusters of the batch-queue kernel that can be resident at once (0 if the
-// device cannot launch it).
-int batch_queue_clusters();
-cudaError_t launch_batch_queue(const QueueArgs &q, int clusters, cudaStream_t s);
+// Clusters of `cluster` (8 or 16) blocks of the batch-queue kernel that can be
+// resident at once (0 if the device cannot launch it).
+int batch_queue_clusters(int cluster);
+cudaError_t launch_batch_queue(const QueueArgs &q, int cluster, int clusters, cudaStream_t s);
 
 // The flooding kernels keep two copies of the a->v messages: a2v in the
 // factor-major (edge id) order every other part of the library uses, and

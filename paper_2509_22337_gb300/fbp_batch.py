@@ -16,12 +16,13 @@ class fbp_graph_desc(C.Structure):
 
 
 class fbp_batch_config(C.Structure):
-    _fields_ = [("one_launch", C.c_int32)]
+    _fields_ = [("one_launch", C.c_int32), ("static_queue", C.c_int32)]
 
 
 class fbp_batch_tuning(C.Structure):
     _fields_ = [("engine_grid", C.c_int32), ("engine_cluster", C.c_int32), ("flood_hub_min", C.c_int32),
-                ("flood_chunk", C.c_int32), ("engine_fuse_lanes", C.c_int32), ("engine_solo_lanes", C.c_int32)]
+                ("flood_chunk", C.c_int32), ("engine_fuse_lanes", C.c_int32), ("engine_solo_lanes", C.c_int32),
+                ("queue_clusters", C.c_int32)]
 
 
 def bind(L) -> None:
@@ -48,10 +49,12 @@ def bind(L) -> None:
     S.bind(L)
 
 
-def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=None, one_launch=None):
+def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=None, one_launch=None,
+                     static_queue=None):
     """graphs: list of FactorGraph; schedules: list of strategy names; max_iters,
-    tols: per-graph lists; one_launch: None (the library's default), True
-    (one persistent launch) or False (two streams).  Returns the handle."""
+    tols: per-graph lists; one_launch / static_queue: the form of the batch
+    (include/fbp_batch.h; None for both = the library's default).  Returns the
+    handle."""
     L = F.load()
     n = len(graphs)
     descs = (fbp_graph_desc * max(n, 1))()
@@ -70,7 +73,9 @@ def fbp_batch_create(graphs, schedules, max_iters, tols, alloc="torch", stream=N
             F._default_alloc = F.torch_allocator()
         alloc = F._default_alloc
     out = C.c_void_p()
-    cfg = None if one_launch is None else fbp_batch_config(1 if one_launch else 0)
+    cfg = None
+    if one_launch is not None or static_queue is not None:
+        cfg = fbp_batch_config(1 if one_launch else 0, 0 if static_queue is False else 1)
     F._check(L.fbp_batch_create_ex(n, C.addressof(descs), None if alloc is None else C.addressof(alloc),
                                    F._stream_ptr(stream), None if cfg is None else C.addressof(cfg), C.byref(out)))
     return out.value
@@ -104,9 +109,9 @@ def fbp_batch_reset(b):
 
 
 def fbp_batch_set_tuning(b, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0, engine_fuse_lanes=-1,
-                         engine_solo_lanes=-1):
+                         engine_solo_lanes=-1, queue_clusters=0):
     t = fbp_batch_tuning(int(engine_grid), int(engine_cluster), int(flood_hub_min), int(flood_chunk),
-                         int(engine_fuse_lanes), int(engine_solo_lanes))
+                         int(engine_fuse_lanes), int(engine_solo_lanes), int(queue_clusters))
     return F._check(F.load().fbp_batch_set_tuning(b, C.addressof(t)))
 
 
@@ -124,11 +129,16 @@ def fbp_batch_destroy(b):
 class Batch:
     """Owner of one batch handle."""
 
-    def __init__(self, graphs, schedules, max_iters, tols, stream=None, one_launch=None):
+    def __init__(self, graphs, schedules, max_iters, tols, stream=None, one_launch=None, static_queue=None):
         self.graphs = graphs
         self.n = len(graphs)
-        self.h = fbp_batch_create(graphs, schedules, max_iters, tols, stream=stream, one_launch=one_launch)
+        self.h = fbp_batch_create(graphs, schedules, max_iters, tols, stream=stream, one_launch=one_launch,
+                                  static_queue=static_queue)
         self.one_launch = bool(F.load().fbp_batch_one_launch(self.h))
+        # the form's name for the tuner: static members in the member queue
+        # unless asked otherwise (the library falls back to the level engine
+        # where the queue cannot launch; the queue's knobs are then no-ops)
+        self.form = "one" if self.one_launch else ("engine" if static_queue is False else "queue")
 
     def run(self):
         return fbp_batch_run(self.h, self.n)
@@ -143,9 +153,9 @@ class Batch:
         return fbp_batch_reset(self.h)
 
     def tune(self, engine_grid=0, engine_cluster=0, flood_hub_min=0, flood_chunk=0, engine_fuse_lanes=-1,
-             engine_solo_lanes=-1):
+             engine_solo_lanes=-1, queue_clusters=0):
         return fbp_batch_set_tuning(self.h, engine_grid, engine_cluster, flood_hub_min, flood_chunk,
-                                    engine_fuse_lanes, engine_solo_lanes)
+                                    engine_fuse_lanes, engine_solo_lanes, queue_clusters)
 
     def stats(self):
         return fbp_batch_get_stats(self.h)

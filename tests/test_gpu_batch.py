@@ -2,7 +2,8 @@
 member, exactly what a single-graph run of it gives (same iterations, same
 messages, same marginals), and match the FP64 oracle like a single run; in
 both of its forms (one persistent launch of thread-block clusters taking
-members from a queue, and the two-stream form)."""
+members from a queue; static members in that queue beside the whole-GPU
+flooding kernels; static members in one level-engine launch beside them)."""
 import numpy as np
 import pytest
 
@@ -10,6 +11,9 @@ from oracle import oracle as O
 from paper_2509_22337_gb300 import gen
 
 pytestmark = pytest.mark.gpu
+
+FORMS = [pytest.param(True, None, id="one_launch"), pytest.param(False, True, id="static_queue"),
+         pytest.param(False, False, id="engine")]
 
 
 def _mixed_graphs():
@@ -36,11 +40,11 @@ def _mixed_graphs():
     return gs, sch, mi, tol
 
 
-@pytest.mark.parametrize("one_launch", [True, False])
-def test_batch_equals_single_runs(fbp, one_launch):
+@pytest.mark.parametrize("one_launch,static_queue", FORMS)
+def test_batch_equals_single_runs(fbp, one_launch, static_queue):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs, sch, mi, tol = _mixed_graphs()
-    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch, static_queue=static_queue)
     assert bt.one_launch == one_launch
     rc, iters, res, status = bt.run()
     if one_launch:  # the whole batch: the queue kernel and the refresh of the flooding members' copy
@@ -61,14 +65,15 @@ def test_batch_equals_single_runs(fbp, one_launch):
     bt.close()
 
 
-@pytest.mark.parametrize("engine_cluster", [1, 16])
-def test_batch_tuning_does_not_change_results(fbp, engine_cluster):
+@pytest.mark.parametrize("static_queue,engine_cluster,queue_clusters",
+                         [(False, 1, 0), (False, 16, 0), (True, 8, 1), (True, 16, 3), (True, 8, 1 << 20)])
+def test_batch_tuning_does_not_change_results(fbp, static_queue, engine_cluster, queue_clusters):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs, sch, mi, tol = _mixed_graphs()
-    ref = B.Batch(gs, sch, mi, tol, one_launch=False)
+    ref = B.Batch(gs, sch, mi, tol, one_launch=False, static_queue=False)
     ref.run()
-    bt = B.Batch(gs, sch, mi, tol, one_launch=False)
-    bt.tune(engine_grid=0, engine_cluster=engine_cluster)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=False, static_queue=static_queue)
+    bt.tune(engine_grid=0, engine_cluster=engine_cluster, queue_clusters=queue_clusters)
     bt.run()
     for i in range(len(gs)):
         assert np.array_equal(ref.messages(i), bt.messages(i)), i
@@ -76,14 +81,14 @@ def test_batch_tuning_does_not_change_results(fbp, engine_cluster):
     bt.close()
 
 
-@pytest.mark.parametrize("one_launch", [True, False])
-def test_batch_members_match_oracle(fbp, one_launch):
+@pytest.mark.parametrize("one_launch,static_queue", FORMS)
+def test_batch_members_match_oracle(fbp, one_launch, static_queue):
     from paper_2509_22337_gb300 import fbp_batch as B
     gs = [gen.tiny(), gen.smartfl(n_layers=15, width=40, seed=77), gen.bingo(n_tuples=500, seed=78)]
     sch = ["PARALL", "TOPO_FB", "PARALL"]
     mi = [50, 30, 20]
     tol = [0.0, 0.0, 0.0]
-    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch, static_queue=static_queue)
     rc, iters, res, status = bt.run()
     for i, g in enumerate(gs):
         o = O.Oracle(g)
@@ -96,14 +101,14 @@ def test_batch_members_match_oracle(fbp, one_launch):
     bt.close()
 
 
-@pytest.mark.parametrize("one_launch", [True, False])
-def test_batch_single_kind_and_empty_member(fbp, one_launch):
+@pytest.mark.parametrize("one_launch,static_queue", FORMS)
+def test_batch_single_kind_and_empty_member(fbp, one_launch, static_queue):
     from paper_2509_22337_gb300 import fbp_batch as B
     empty = gen.FactorGraph(4, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint8),
                             np.zeros(0, np.float32), np.array([0.2, np.nan, 0.7, np.nan], np.float32),
                             np.full(4, -1, np.int8), "empty")
     gs = [gen.smartfl(n_layers=8, width=30, seed=5), empty, gen.smartfl(n_layers=6, width=20, seed=6)]
-    bt = B.Batch(gs, ["TOPO_FB"] * 3, [20, 20, 20], [1e-6] * 3, one_launch=one_launch)
+    bt = B.Batch(gs, ["TOPO_FB"] * 3, [20, 20, 20], [1e-6] * 3, one_launch=one_launch, static_queue=static_queue)
     rc, iters, res, status = bt.run()
     np.testing.assert_allclose(bt.marginals(1), [0.2, 0.5, 0.7, 0.5], atol=1e-7)
     assert iters[1] == 1
@@ -124,8 +129,8 @@ def test_many_graphs_of_different_sizes_interleaved(fbp):
     Bh.close()
 
 
-@pytest.mark.parametrize("one_launch", [True, False])
-def test_batch_autotuner(fbp, tmp_path, monkeypatch, one_launch):
+@pytest.mark.parametrize("one_launch,static_queue", FORMS)
+def test_batch_autotuner(fbp, tmp_path, monkeypatch, one_launch, static_queue):
     """The batch tuner picks one of its candidates, and the tuned batch
     computes what the untuned one does, bit for bit for every member (no
     launch shape changes the arithmetic); a second call answers from the
@@ -133,11 +138,11 @@ def test_batch_autotuner(fbp, tmp_path, monkeypatch, one_launch):
     from paper_2509_22337_gb300 import autotune, fbp_batch as B
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     gs, sch, mi, tol = _mixed_graphs()
-    ref = B.Batch(gs, sch, mi, tol, one_launch=False)
+    ref = B.Batch(gs, sch, mi, tol, one_launch=False, static_queue=False)
     ref.run()
-    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch)
+    bt = B.Batch(gs, sch, mi, tol, one_launch=one_launch, static_queue=static_queue)
     best = autotune.tune_batch(bt, gs, sch)
-    assert best in list(autotune.batch_candidates())
+    assert best in list(autotune.batch_candidates(bt.form))
     bt.reset()
     bt.run()
     for i in range(len(gs)):
@@ -146,3 +151,20 @@ def test_batch_autotuner(fbp, tmp_path, monkeypatch, one_launch):
     assert autotune.tune_batch(bt, gs, sch) == best
     ref.close()
     bt.close()
+
+
+def test_one_launch_cluster_sizes_agree(fbp):
+    """The one-launch form with 8-block and 16-block clusters computes the
+    same messages, iterations and residuals (a cluster only carries a member)."""
+    from paper_2509_22337_gb300 import fbp_batch as B
+    gs, sch, mi, tol = _mixed_graphs()
+    runs = []
+    for cluster in (8, 16):
+        bt = B.Batch(gs, sch, mi, tol, one_launch=True)
+        bt.tune(engine_cluster=cluster)
+        rc, iters, res, status = bt.run()
+        runs.append(([bt.messages(i) for i in range(len(gs))], iters, res))
+        bt.close()
+    (m8, i8, r8), (m16, i16, r16) = runs
+    assert np.array_equal(i8, i16) and np.array_equal(np.float32(r8), np.float32(r16))
+    assert all(np.array_equal(a, b) for a, b in zip(m8, m16))

@@ -781,7 +781,7 @@ def run_gpu(args):
         # the unit is one flooding iteration (its five kernels, replayed from
         # a captured CUDA graph): algorithmic bytes per iteration over the
         # device time per iteration
-        kname = "flooding iteration (k_sub_products, k_beliefs, k_a2v_lanes, k_flood_check)"
+        kname = "flooding iteration (k_beliefs, k_row_beliefs, k_a2v_lanes, k_flood_check)"
         kkey = "flood"
         launches_per_step = max(sweeps, 1)
         bytes_per_launch = pair_model_bytes_per_pass(g)

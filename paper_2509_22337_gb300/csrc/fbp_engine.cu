@@ -754,11 +754,12 @@ __global__ void __launch_bounds__(kQueueBlock, 3) k_batch_queue(const QueueArgs 
         for (it = 1; !empty_static && it <= max_iters; ++it) {
             float rmax = 0.f;
             if (kind == 0) {
+                // the sub-chunk products and the short rows' beliefs share no data
                 for (int k = M.sub0 + gt; k < M.sub1; k += nt) fdev::sub_product_item<true>(Q.g, Q.F, Q.a2v_vm, k);
-                if ((failed = bar.sync())) break;
                 for (int v = M.v0 + gt; v < M.v1; v += nt) fdev::belief_var_item<true>(Q.g, Q.F, Q.a2v_vm, v);
+                if ((failed = bar.sync())) break;
                 for (int w = M.med0 + gt; w < M.med1; w += nt) fdev::belief_medium_item<true>(Q.g, Q.F, w);
-                for (int hr = M.hub0 + gw; hr < M.hub1; hr += nwp) fdev::belief_hub_warp<true>(Q.g, Q.F, hr);
+                for (int hr = M.hub0 + gw; hr < M.hub1; hr += nwp) fdev::belief_hub_warp<true, 2>(Q.g, Q.F, hr);
                 if ((failed = bar.sync())) break;
                 if (M.wide1 > M.wide0) {
                     for (int k = M.wide0 + gt; k < M.wide1; k += nt) fdev::wide_v2a_item<true>(Q.g, Q.F, Q.a2v, k);
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(kQueueBlock, 3) k_batch_queue(const QueueArgs 
                 for (int w = M.tw0 + gw; w < M.tw1; w += nwp) {
                     float dd = 0.f;
                     int graph = -1;
-                    fdev::lanes_warp<true>(Q.g, Q.F, Q.a2v, Q.a2v_vm, w, dd, ng, graph);
+                    fdev::lanes_warp<true, 0>(Q.g, Q.F, Q.a2v, Q.a2v_vm, w, dd, ng, graph);
                     rmax = fmaxf(rmax, dd);
                 }
                 for (int k = M.wide0 + gt; k < M.wide1; k += nt) {

@@ -12,8 +12,9 @@
 // underflows: each of the two entries is kept as a mantissa and an integer
 // exponent while the row is reduced.
 //   rows of degree <= 8       one thread per row, entries in row order
-//   longer rows               one thread per 32-entry sub-chunk; a row of
-//                             2..8 sub-chunks (at most FBP_OPT_FLOOD_HUB_MIN
+//   longer rows               one thread per 32-entry sub-chunk (in the same
+//                             launch as the short rows); then a row of 2..8
+//                             sub-chunks (at most FBP_OPT_FLOOD_HUB_MIN
 //                             entries) combined by one thread, a longer one
 //                             by one warp
 // The product of every row longer than 8 entries is grouped one way only,
@@ -59,35 +60,40 @@ __global__ void k_sync_vm(const DevGraph g, const float *__restrict__ a2v, float
     if (k < g.ne) a2v_vm[k] = a2v[__ldg(g.vedge + k)];
 }
 
-// Products of the 32-entry sub-chunks of the rows longer than 8 entries, one
-// thread per sub-chunk; a row of one sub-chunk gets its belief here.
-__global__ void __launch_bounds__(256) k_sub_products(const DevGraph g, FloodPlanDev F,
-                                                      const float *__restrict__ a2v_vm)
+// Phase 1, first pass (two roles that share no data, so the long per-thread
+// product chains of the sub-chunks overlap with the short rows' loads).
+// Blocks [0, nb_subs): the products of the 32-entry sub-chunks of the rows
+// longer than 8 entries, sub_threads per block, one thread per sub-chunk (a
+// row of one sub-chunk gets its belief here).  The nb_vars blocks from
+// nb_subs on: the belief of every variable of degree <= 8, one thread per
+// variable, each thread taking variables a grid of those blocks apart.
+__global__ void __launch_bounds__(256, 8) k_beliefs(const DevGraph g, FloodPlanDev F, const float *__restrict__ a2v_vm)
 {
     if (*(volatile const int *)F.done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < F.n_subs) sub_product_item<false>(g, F, a2v_vm, k);
+    const int nb_subs = (F.n_subs + F.sub_threads - 1) / F.sub_threads;
+    const int b = blockIdx.x;
+    if (b < nb_subs) {
+        const int k = b * F.sub_threads + threadIdx.x;
+        if (threadIdx.x < F.sub_threads && k < F.n_subs) sub_product_item<false>(g, F, a2v_vm, k);
+        return;
+    }
+    belief_var_loop(g, F, a2v_vm, (b - nb_subs) * blockDim.x + threadIdx.x, F.nb_vars * blockDim.x);
 }
 
-// Beliefs.  Blocks [0, nb_vars): one thread per variable of degree <= 8;
-// then one thread per medium row; then one warp per hub row (both combine
-// sub-chunk products of k_sub_products).
-__global__ void __launch_bounds__(256) k_beliefs(const DevGraph g, FloodPlanDev F, const float *__restrict__ a2v_vm)
+// Phase 1, second pass: the rows of several sub-chunks combine their
+// sub-chunk products.  Blocks [0, nb_medium): one thread per medium row;
+// then one warp per hub row.
+__global__ void __launch_bounds__(256) k_row_beliefs(const DevGraph g, FloodPlanDev F)
 {
     if (*(volatile const int *)F.done) return;
     const int b = blockIdx.x;
-    if (b < F.nb_vars) {
-        const int v = b * blockDim.x + threadIdx.x;
-        if (v < g.nv) belief_var_item<false>(g, F, a2v_vm, v);
-        return;
-    }
-    if (b < F.nb_vars + F.nb_medium) {
-        const int w = (b - F.nb_vars) * blockDim.x + threadIdx.x;
+    if (b < F.nb_medium) {
+        const int w = b * blockDim.x + threadIdx.x;
         if (w < F.n_medium) belief_medium_item<false>(g, F, w);
         return;
     }
-    const int hr = (b - F.nb_vars - F.nb_medium) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (hr < F.n_hub_rows) belief_hub_warp<false>(g, F, hr);
+    const int hr = (b - F.nb_medium) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (hr < F.n_hub_rows) belief_hub_warp<false, 8>(g, F, hr);
 }
 
 // ----------------------------------------------------------------------------
@@ -96,6 +102,8 @@ __global__ void __launch_bounds__(256) k_beliefs(const DevGraph g, FloodPlanDev 
 // Typed factors of at most 32 variables: one lane per message, whole
 // consecutive factors per warp (lanes_warp); the iteration's residual is
 // reduced per block into one of kResSlots words (per graph in a batch).
+// One instantiation per combination of lanes_warp's optional parts.
+template <int kFeat>
 __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
                                                    float *__restrict__ a2v_vm, IterCtl ctl)
 {
@@ -104,9 +112,9 @@ __global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const Flood
     float dd = 0.f;
     unsigned long long ng = 0;
     int graph = -1;
-    if (w < F.n_twarps) lanes_warp<false>(g, F, a2v, a2v_vm, w, dd, ng, graph);  // warp-uniform
+    if (w < F.n_twarps) lanes_warp<false, kFeat>(g, F, a2v, a2v_vm, w, dd, ng, graph);  // warp-uniform
     if (ng) atomicAdd(ctl.guards, ng);
-    if (F.batch.n_graphs > 0) {
+    if constexpr ((kFeat & kFeatBatch) != 0) {
         batch_residual(F, graph, dd);
         return;
     }
@@ -301,11 +309,26 @@ __global__ void k_flood_check(unsigned *slots, unsigned *hist, float tol, int *c
 // Phase 1 and phase 2 of one iteration (or one RESIDUAL level).
 void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a2v_vm, IterCtl ctl, cudaStream_t s)
 {
-    if (P.n_subs > 0) k_sub_products<<<(P.n_subs + P.sub_threads - 1) / P.sub_threads, P.sub_threads, 0, s>>>(g, P, a2v_vm);
-    const int nb = P.nb_vars + P.nb_medium + (P.n_hub_rows + 7) / 8;
-    if (nb > 0) k_beliefs<<<nb, 256, 0, s>>>(g, P, a2v_vm);
+    const int nb1 = (P.n_subs + P.sub_threads - 1) / P.sub_threads + P.nb_vars;
+    if (nb1 > 0) k_beliefs<<<nb1, 256, 0, s>>>(g, P, a2v_vm);
+    const int nb2 = P.nb_medium + (P.n_hub_rows + 7) / 8;
+    if (nb2 > 0) k_row_beliefs<<<nb2, 256, 0, s>>>(g, P);
     if (P.n_wide > 0) k_wide_v2a<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v);
-    if (P.n_twarps > 0) k_a2v_lanes<<<(P.n_twarps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
+    if (P.n_twarps > 0) {
+        const int feat = (P.batch.n_graphs > 0 ? kFeatBatch : 0) | (P.elevel ? kFeatLevel : 0) | (P.dres ? kFeatDres : 0);
+        decltype(&k_a2v_lanes<0>) k = nullptr;
+        switch (feat) {
+        case 0: k = k_a2v_lanes<0>; break;
+        case 1: k = k_a2v_lanes<1>; break;
+        case 2: k = k_a2v_lanes<2>; break;
+        case 3: k = k_a2v_lanes<3>; break;
+        case 4: k = k_a2v_lanes<4>; break;
+        case 5: k = k_a2v_lanes<5>; break;
+        case 6: k = k_a2v_lanes<6>; break;
+        default: k = k_a2v_lanes<7>; break;
+        }
+        k<<<(P.n_twarps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
+    }
     if (P.n_warps > 0) k_a2v_fused<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
     if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
 }
@@ -362,7 +385,7 @@ cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, 
 
 int flood_launches(const DevGraph &g, const FloodPlanDev &F)
 {
-    return (F.n_subs > 0) + (F.nb_vars + F.nb_medium + F.n_hub_rows > 0) + 2 * (F.n_wide > 0) + (F.n_twarps > 0) +
+    return (F.n_subs + F.nb_vars > 0) + (F.nb_medium + F.n_hub_rows > 0) + 2 * (F.n_wide > 0) + (F.n_twarps > 0) +
            (F.n_warps > 0) + 1;
 }
 

@@ -25,7 +25,7 @@ constexpr int kFloodChunk = 8;         // iterations per captured CUDA graph
 
 struct FloodPlanDev {
     // phase 1 (beliefs, variable-major): every variable of degree <= 8 one
-    // thread (blocks 0 .. nb_vars-1); every longer row in 32-entry
+    // thread (nb_vars blocks stepping through the variables); every longer row in 32-entry
     // sub-chunks, one thread each (a row of one sub-chunk writes its belief
     // there); then one thread per medium row (2..8 sub-chunks) or one warp per
     // hub row combines the sub-chunk products

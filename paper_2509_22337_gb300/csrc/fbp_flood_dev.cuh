@@ -132,51 +132,54 @@ __device__ __forceinline__ XP warp_product(XP t)
 //       without the own message" as well as any larger count).
 __device__ __forceinline__ uint2 belief_pack(const XP &t)
 {
-    const float q = t.m0 * rcp_approx(t.m1);  // within a few ulp of the quotient
+    const float q = t.m0 * rcp_normal(t.m1);  // within a few ulp of the quotient
     const int de = max(-(1 << 26), min(1 << 26, t.e0 - t.e1));
     return make_uint2(__float_as_uint(q), (unsigned)(de * 16 + min(t.z0, 2) * 4 + min(t.z1, 2)));
 }
 
-// r * 2^E by two exact power-of-two factors (each exponent clamped to the
-// normal range), so a result in the normal range rounds once; far outside it
-// the result saturates to 0 or infinity, as the exact one would in FP32.
-__device__ __forceinline__ float scale2(float r, int E)
+// t * 2^k for t in (1/4, 4) and k <= 1.  While 2^k is normal this is one
+// multiplication by it (exact unless the result is subnormal, where it rounds
+// once); below that, two (k is clamped at -300, where every result is 0).
+__device__ __forceinline__ float scale_down(float t, int k)
 {
-    E = max(-300, min(300, E));
-    const int e1 = E / 2, e2 = E - e1;
-    r *= __int_as_float((127 + max(-126, min(127, e1))) << 23);
-    return r * __int_as_float((127 + max(-126, min(127, e2))) << 23);
+    k = max(k, -300);
+    const int k1 = max(k, -126), k2 = max(k - k1, -126);
+    return t * __int_as_float((127 + k1) << 23) * __int_as_float((127 + k2) << 23);
 }
 
 // v->a message of an edge whose variable has belief record b and whose own
 // incoming a->v message is rho (Eq. 1: phi times every other incoming
 // message, i.e. the belief without the own message), encoded; zero mass
 // becomes the uniform message.  With the own message's entries x0, x1 the
-// result's ratio is (b0/b1) / (x0/x1); a zero own entry was counted in the
-// belief rather than multiplied, so it divides out as 1.  Mantissas and
-// exponents are split with integer operations; quotients go through the
-// approximate reciprocal (a few ulp).
+// result's ratio is (b0/b1) / (x0/x1) = t 2^E with t in (1/4, 4); a zero own
+// entry was counted in the belief rather than multiplied, so it divides out
+// as 1.  Mantissas and exponents are split with integer operations; the
+// quotient and the final reciprocal go through the approximate reciprocal
+// (a few ulp) of a number in (1/4, 4).
 __device__ __forceinline__ float v2a_from_belief(uint2 b, float rho)
 {
     const int w = (int)b.y;
     const float a = fabsf(rho);
     const bool neg = signbit(rho);  // own message (1, a), else (a, 1)
-    const int z0 = ((w >> 2) & 3) - (!neg && a == 0.f);
-    const int z1 = (w & 3) - (neg && a == 0.f);
-    if (z0 > 0 && z1 > 0) return 1.f;  // zero mass: uniform
-    if (z0 > 0) return 0.f;            // hard (0, 1)
-    if (z1 > 0) return -0.f;           // hard (1, 0)
-    float r = __uint_as_float(b.x);    // in (1/2, 2)
+    float t = __uint_as_float(b.x);  // in (1/2, 2)
     int E = w >> 4;
-    if (a != 0.f) {
+    if ((w & 15) != 0 || a == 0.f) {  // zeros counted, or a hard own message
+        const int z0 = ((w >> 2) & 3) - (!neg && a == 0.f);
+        const int z1 = (w & 3) - (neg && a == 0.f);
+        if (z0 > 0 && z1 > 0) return 1.f;  // zero mass: uniform
+        if (z0 > 0) return 0.f;            // hard (0, 1)
+        if (z1 > 0) return -0.f;           // hard (1, 0)
+        // here a == 0: the own zero entry divides out
+    } else {
         int ea;
         const float ma = split(a, ea);  // [1, 2)
-        r = neg ? r * ma : r * rcp_approx(ma);
+        t = neg ? t * ma : t * rcp_normal(ma);
         E += neg ? ea : -ea;
     }
-    r = scale2(r, E);
-    if (r <= 1.f) return r;            // m1 is the larger entry
-    return -rcp_approx(r);             // m0 is the larger entry
+    // the ratio t 2^E is at most 1 iff t 2^clamp(E, -2, 2) is (t lies in (1/4, 4))
+    const bool le = t * __int_as_float((127 + max(-2, min(2, E))) << 23) <= 1.f;
+    const float r = scale_down(le ? t : rcp_normal(t), le ? E : -E);
+    return le ? r : -r;  // m1 the larger entry, else m0
 }
 
 template <bool kC>
@@ -203,19 +206,34 @@ __device__ __forceinline__ XP ldx(const XP *p)
 }
 
 // Product of entries x[b, end) in order (at most one sub-chunk), one thread;
-// every load is issued first.  Entries past the warp's longest run are
+// entries load in groups of four, each group while the one before it
+// multiplies (few registers: this shares a launch with latency-bound work
+// that wants every warp slot).  Entries past the warp's longest run are
 // skipped by a uniform branch (a padded entry would multiply by exactly 1).
 template <bool kC>
 __device__ __forceinline__ XP seq_product(const float *__restrict__ x, int b, int end)
 {
-    float r[kFloodSub];
-#pragma unroll
-    for (int u = 0; u < kFloodSub; ++u) r[u] = b + u < end ? ldm<kC>(x + b + u) : 1.f;
+    constexpr int kG = 4;
     const int nw = __reduce_max_sync(__activemask(), end - b);
+    float r[kG], nx[kG];
+#pragma unroll
+    for (int u = 0; u < kG; ++u) r[u] = b + u < end ? ldm<kC>(x + b + u) : 1.f;
     XP t = xp_one();
 #pragma unroll
-    for (int u = 0; u < kFloodSub; ++u)
-        if (u < nw) xmul(t, r[u]);
+    for (int gi = 0; gi < kFloodSub / kG; ++gi) {
+        const int c = b + (gi + 1) * kG;  // first entry of the next group
+#pragma unroll
+        for (int u = 0; u < kG; ++u) nx[u] = 1.f;
+        if (gi + 1 < kFloodSub / kG && (gi + 1) * kG < nw) {
+#pragma unroll
+            for (int u = 0; u < kG; ++u) nx[u] = c + u < end ? ldm<kC>(x + c + u) : 1.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kG; ++u)
+            if (gi * kG + u < nw) xmul(t, r[u]);
+#pragma unroll
+        for (int u = 0; u < kG; ++u) r[u] = nx[u];
+    }
     return t;
 }
 
@@ -243,13 +261,9 @@ __device__ __forceinline__ void sub_product_item(const DevGraph &g, const FloodP
 // order.  Slots past the longest row among the calling warp's active lanes
 // are skipped by a uniform branch (a padded slot would multiply by exactly 1).
 template <bool kC>
-__device__ __forceinline__ void belief_var_item(const DevGraph &g, const FloodPlanDev &F,
-                                                const float *__restrict__ a2v_vm, int v)
+__device__ __forceinline__ void belief_short_row(const FloodPlanDev &F, const float *__restrict__ a2v_vm, int v, int lo,
+                                                 int d, float phi)
 {
-    if (var_frozen(F, v)) return;
-    const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
-    if (d > kFloodSmallMax) return;  // a row of sub-chunks
-    const float phi = __ldg(g.phi + v);
     const int dw = __reduce_max_sync(__activemask(), d);
     float r[kFloodSmallMax];
 #pragma unroll
@@ -264,6 +278,45 @@ __device__ __forceinline__ void belief_var_item(const DevGraph &g, const FloodPl
         if (u < dw) xmul(t, r[u]);
     xmul(t, phi);
     F.belief[v] = belief_pack(t);
+}
+
+template <bool kC>
+__device__ __forceinline__ void belief_var_item(const DevGraph &g, const FloodPlanDev &F,
+                                                const float *__restrict__ a2v_vm, int v)
+{
+    if (var_frozen(F, v)) return;
+    const int lo = __ldg(g.vptr + v), d = __ldg(g.vptr + v + 1) - lo;
+    if (d > kFloodSmallMax) return;  // a row of sub-chunks
+    belief_short_row<kC>(F, a2v_vm, v, lo, d, __ldg(g.phi + v));
+}
+
+// The same for variables v, v + stride, ... below g.nv, one thread: the next
+// variable's row bounds and phi load while this one's row multiplies.
+__device__ __forceinline__ void belief_var_loop(const DevGraph &g, const FloodPlanDev &F,
+                                                const float *__restrict__ a2v_vm, int v, int stride)
+{
+    int lo = 0, d = 0;
+    float phi = 1.f;
+    if (v < g.nv) {
+        lo = __ldg(g.vptr + v);
+        d = __ldg(g.vptr + v + 1) - lo;
+        phi = __ldg(g.phi + v);
+    }
+    while (v < g.nv) {
+        const int vn = v + stride;
+        int lo_n = 0, d_n = 0;
+        float phi_n = 1.f;
+        if (vn < g.nv) {
+            lo_n = __ldg(g.vptr + vn);
+            d_n = __ldg(g.vptr + vn + 1) - lo_n;
+            phi_n = __ldg(g.phi + vn);
+        }
+        if (d <= kFloodSmallMax && !var_frozen(F, v)) belief_short_row<false>(F, a2v_vm, v, lo, d, phi);
+        v = vn;
+        lo = lo_n;
+        d = d_n;
+        phi = phi_n;
+    }
 }
 
 // Medium row w (2..8 sub-chunks): the butterfly over 32 slots of which slots
@@ -297,15 +350,30 @@ __device__ __forceinline__ void belief_medium_item(const DevGraph &g, const Floo
 }
 
 // Hub row hr, one whole warp: lane j combines sub-chunks j, j+32, ... in
-// order, then the xor butterfly.
-template <bool kC>
+// order, then the xor butterfly.  The largest rows have thousands of
+// sub-chunks, so each lane keeps the next kD of its products in flight while
+// it combines (the chain, not the arithmetic, sets this kernel's time; kD
+// only trades registers for that).
+template <bool kC, int kD>
 __device__ __forceinline__ void belief_hub_warp(const DevGraph &g, const FloodPlanDev &F, int hr)
 {
     const int lane = threadIdx.x & 31;
     const int4 row = __ldg(F.hub_row + hr);  // {variable, first agg slot, sub-chunks, 0}
     if (var_frozen(F, row.x)) return;        // warp-uniform
+    const XP *P = F.agg + row.y;
+    const int n = row.z;
+    XP buf[kD];
+#pragma unroll
+    for (int d = 0; d < kD; ++d) buf[d] = lane + 32 * d < n ? ldx<kC>(P + lane + 32 * d) : xp_one();
     XP t = xp_one();
-    for (int j = lane; j < row.z; j += 32) t = xcombine(t, ldx<kC>(F.agg + row.y + j));
+    for (int base = 0; base < n; base += 32 * kD) {  // warp-uniform
+#pragma unroll
+        for (int d = 0; d < kD; ++d) {
+            const int j = base + 32 * d + lane, jn = j + 32 * kD;
+            if (j < n) t = xcombine(t, buf[d]);
+            if (jn < n) buf[d] = ldx<kC>(P + jn);
+        }
+    }
     t = warp_product(t);
     if (lane == 0) {
         xmul(t, __ldg(g.phi + row.x));
@@ -348,9 +416,17 @@ __device__ __forceinline__ void batch_residual(const FloodPlanDev &F, int graph,
 //   EQ           every variable is a "premise", s_j replaced by m_j0:
 //                to variable i (Y, X) = (prod_{u != i} m_u0, prod_{u != i} m_u1)
 // Messages enter scaled so that their larger entry is 1, so Y <= 2^31.
+// Each lane decodes its own v->a message once (flipped for OR) and the
+// others' arrive decoded by shuffle.
 // Called by a whole warp with the same w; returns the lane's |dP(x=1)| in dd
-// (0 for no write), its guard count in ng and (batch) its graph.
-template <bool kC>
+// (0 for no write), its guard count in ng and (batch) its graph.  kFeat
+// selects the optional parts: kFeatBatch (a batched union: factors of
+// finished graphs are skipped, graph returned), kFeatLevel (one level of a
+// device-scheduled RESIDUAL iteration: only edges with F.elevel[e] ==
+// F.level are written), kFeatDres (each written edge's |dP| is recorded in
+// F.dres).
+constexpr int kFeatBatch = 1, kFeatLevel = 2, kFeatDres = 4;
+template <bool kC, int kFeat>
 __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev &F, float *__restrict__ a2v,
                                            float *__restrict__ a2v_vm, int w, float &dd, unsigned long long &ng,
                                            int &graph)
@@ -364,7 +440,7 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
         fst = __ldg(g.fptr + wr.z + lane) - wr.x;
         ftyp = __ldg(g.ftype + wr.z + lane);
         fpar = __ldg(g.fparam + wr.z + lane);
-        if (F.batch.n_graphs > 0) fgr = __ldg(F.fgraph + wr.z + lane);
+        if constexpr ((kFeat & kFeatBatch) != 0) fgr = __ldg(F.fgraph + wr.z + lane);
     }
     const unsigned starts = __reduce_or_sync(0xffffffffu, lane < nf ? 1u << fst : 0u);
     const unsigned upto = starts & (0xffffffffu >> (31 - lane));  // factor starts at or before this lane
@@ -381,7 +457,7 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
     float x = 1.f, old = 1.f;
     int slot = 0;
     bool frozen = false;
-    if (F.batch.n_graphs > 0) {
+    if constexpr ((kFeat & kFeatBatch) != 0) {
         graph = __shfl_sync(0xffffffffu, fgr, fi);
         frozen = __ldcg(F.batch.done + graph) != 0;
     }
@@ -393,20 +469,24 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
     } else {
         graph = -1;
     }
-    // the output's message (flipped with the inputs for OR)
-    P2 my = dec(__shfl_sync(0xffffffffu, x, (first + n - 1) & 31));
-    if (fin) my = P2{my.m1, my.m0};
+    // this lane's message decoded (flipped with the inputs for OR), and the
+    // entry that multiplies Y
+    P2 me = dec(x);
+    if (fin) me = P2{me.m1, me.m0};
+    const float ey_me = eq ? me.m0 : me.m0 + me.m1;
+    // the output's message
+    const int last = (first + n - 1) & 31;
+    P2 my{__shfl_sync(0xffffffffu, me.m0, last), __shfl_sync(0xffffffffu, me.m1, last)};
     if (eq) my = P2{1.f, 1.f};
     float X = 1.f, Y = 1.f, D = 0.f;
     const int span = __reduce_max_sync(0xffffffffu, valid ? np : 0);
     for (int j = 0; j < span; ++j) {
-        const float r = __shfl_sync(0xffffffffu, x, (first + j) & 31);
+        const int src = (first + j) & 31;
+        const float m0 = __shfl_sync(0xffffffffu, me.m0, src), m1 = __shfl_sync(0xffffffffu, me.m1, src);
+        const float ey = __shfl_sync(0xffffffffu, ey_me, src);
         if (j < np && j != i) {
-            P2 m = dec(r);
-            if (fin) m = P2{m.m1, m.m0};
-            const float ey = eq ? m.m0 : m.m0 + m.m1;
-            D = fmaf(D, ey, X * m.m0);
-            X *= m.m1;
+            D = fmaf(D, ey, X * m0);
+            X *= m1;
             Y *= ey;
         }
     }
@@ -423,14 +503,16 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
         mu = P2{c0 * Y, fmaf(d0, X, d1 * D)};
     }
     if (fout) mu = P2{mu.m1, mu.m0};
-    if (valid && !frozen && (!F.elevel || __ldg(F.elevel + e) == F.level)) {
+    bool write = valid && !frozen;
+    if constexpr ((kFeat & kFeatLevel) != 0) write = write && __ldg(F.elevel + e) == F.level;
+    if (write) {
         bool gd = false;
         const float r = enc_fast(mu, gd);
         ng += gd;
         dd = delta_p1_fast(r, old);
         __stcs(a2v + e, r);
         a2v_vm[slot] = r;
-        if (F.dres) F.dres[e] = dd;
+        if constexpr ((kFeat & kFeatDres) != 0) F.dres[e] = dd;
     }
 }
 

@@ -282,7 +282,9 @@ int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<
     parallel_for(h.ne, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
         for (int64_t k = b; k < e; ++k) vpos[h.vedge[k]] = (int32_t)k;
     });
-    F.nb_vars = (h.nv + 255) / 256;
+    // the short rows' blocks: one resident grid (8 blocks of 256 per SM)
+    // whose threads step through the variables
+    F.nb_vars = (int32_t)std::min<int64_t>((h.nv + 255) / 256, 8 * (int64_t)num_sms());
     F.n_subs = (int32_t)subs.size();
     F.sub_threads = std::max(32, std::min(256, g->flood_chunk / kFloodSub));
     F.n_medium = (int32_t)medium.size();

@@ -196,17 +196,22 @@ __device__ __forceinline__ P2 a2v_terms(const DevGraph &g, int a, int n, int i, 
     return mu;
 }
 
-// Hardware reciprocal approximation (rcp.approx.f32: relative error within a
-// couple of ulp, denormals kept).
-__device__ __forceinline__ float rcp_approx(float x)
+// Hardware reciprocal approximation with subnormals flushed
+// (rcp.approx.ftz.f32: relative error within a couple of ulp).  Callers pass
+// arguments whose reciprocal is normal as well, where it is the same
+// approximation as the subnormal-keeping form, at a fraction of its cost.
+__device__ __forceinline__ float rcp_normal(float x)
 {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
 // Encoding through the reciprocal of the larger entry (result within a few
-// ulp of the quotient, clamped to |rho| <= 1); zero mass -> uniform.
+// ulp of the quotient, clamped to |rho| <= 1); zero mass -> uniform.  A larger
+// entry outside [2^-64, 2^64] is first brought inside by a power of two,
+// applied to both entries (exact unless the smaller one then leaves the
+// normal range, where the quotient itself is below it).
 __device__ __forceinline__ float enc_fast(P2 m, bool &guard)
 {
     const float s = m.m0 + m.m1;
@@ -214,17 +219,23 @@ __device__ __forceinline__ float enc_fast(P2 m, bool &guard)
         guard = true;
         return 1.f;
     }
-    const float mx = fmaxf(m.m0, m.m1), mn = fminf(m.m0, m.m1);
-    const float r = fminf(mn * rcp_approx(mx), 1.f);
+    float mx = fmaxf(m.m0, m.m1), mn = fminf(m.m0, m.m1);
+    if (!(mx >= 0x1p-64f && mx <= 0x1p64f)) {
+        const float k = mx < 1.f ? 0x1p64f : 0x1p-64f;
+        mx *= k;
+        mn *= k;
+    }
+    const float r = fminf(mn * rcp_normal(mx), 1.f);
     return m.m1 >= m.m0 ? r : -r;
 }
 
-// delta_p1 for the convergence test only: approximate reciprocals (a few ulp).
+// delta_p1 for the convergence test only: approximate reciprocals (a few
+// ulp) of arguments in [1, 4].
 __device__ __forceinline__ float delta_p1_fast(float rn, float ro)
 {
     const float an = fabsf(rn), ao = fabsf(ro);
-    if (signbit(rn) == signbit(ro)) return fabsf(ao - an) * rcp_approx((1.f + an) * (1.f + ao));
-    return (1.f - an) * rcp_approx(2.f * (1.f + an)) + (1.f - ao) * rcp_approx(2.f * (1.f + ao));
+    if (signbit(rn) == signbit(ro)) return fabsf(ao - an) * rcp_normal((1.f + an) * (1.f + ao));
+    return (1.f - an) * rcp_normal(2.f * (1.f + an)) + (1.f - ao) * rcp_normal(2.f * (1.f + ao));
 }
 
 // Raise a max word to `bits` (the bits of a non-negative float, so that the

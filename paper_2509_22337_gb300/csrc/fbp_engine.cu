@@ -722,7 +722,9 @@ struct ClusterBar {
 template <int kCl>
 __global__ void __launch_bounds__(kQueueBlock, 3) k_batch_queue(const QueueArgs Q)
 {
+    static_assert(kQueueBlock == kFloodSlots, "a block combines one hub row");
     __shared__ P2 s_m[kQueueBlock];
+    __shared__ XP s_x[kFloodSlots];
     P2 *sm = s_m + (threadIdx.x & ~31);
     const int r = (int)cluster_ctarank(), c = (int)cluster_id_x();
     const int gt = r * kQueueBlock + (int)threadIdx.x, nt = kCl * kQueueBlock;  // thread in the cluster
@@ -759,7 +761,7 @@ __global__ void __launch_bounds__(kQueueBlock, 3) k_batch_queue(const QueueArgs 
                 for (int v = M.v0 + gt; v < M.v1; v += nt) fdev::belief_var_item<true>(Q.g, Q.F, Q.a2v_vm, v);
                 if ((failed = bar.sync())) break;
                 for (int w = M.med0 + gt; w < M.med1; w += nt) fdev::belief_medium_item<true>(Q.g, Q.F, w);
-                for (int hr = M.hub0 + gw; hr < M.hub1; hr += nwp) fdev::belief_hub_warp<true, 2>(Q.g, Q.F, hr);
+                for (int hr = M.hub0 + r; hr < M.hub1; hr += kCl) fdev::belief_hub_block<true, 1>(Q.g, Q.F, hr, s_x);
                 if ((failed = bar.sync())) break;
                 if (M.wide1 > M.wide0) {
                     for (int k = M.wide0 + gt; k < M.wide1; k += nt) fdev::wide_v2a_item<true>(Q.g, Q.F, Q.a2v, k);

@@ -16,18 +16,19 @@
 //                             launch as the short rows); then a row of 2..8
 //                             sub-chunks (at most FBP_OPT_FLOOD_HUB_MIN
 //                             entries) combined by one thread, a longer one
-//                             by one warp
+//                             by one block of 256 threads
 // The product of every row longer than 8 entries is grouped one way only,
 // whichever kernel carries the row: the row is cut into 32-entry sub-chunks,
-// each multiplied in order; sub-chunk s goes to slot s mod 32 (a slot
-// multiplies its sub-chunks in order), and the 32 slots are combined by an
-// xor butterfly (slot j with slot j^16, then j^8, j^4, j^2, j^1).  A row of at
-// most 256 entries fills slots 0..7 only, and the one-thread combine
-// evaluates exactly that butterfly, so the thread and the warp combines
-// compute the same bits and the split options (FBP_OPT_FLOOD_HUB_MIN,
-// _CHUNK) only move work between kernels.  phi_v is multiplied in last.  Every multiply
-// rounds the exact product once (the mantissa/exponent form never goes
-// subnormal), so only this grouping decides the result.
+// each multiplied in order; sub-chunk s goes to slot s mod 256 (a slot
+// multiplies its sub-chunks in order), and the 256 slots are combined by an
+// xor butterfly (slot j with slot j^128, then j^64, ..., j^2, j^1).  A row of
+// at most 256 entries fills slots 0..7 only, and the one-thread combine
+// evaluates exactly that butterfly (a product with an empty slot is the value
+// itself), so the thread and the block combines compute the same bits and
+// the split options (FBP_OPT_FLOOD_HUB_MIN, _CHUNK) only move work between
+// kernels.  phi_v is multiplied in last.  Every multiply rounds the exact
+// product once (the mantissa/exponent form never goes subnormal), so only
+// this grouping decides the result.
 //
 // Phase 2, the closed-form local-structure messages (Eq. 4).  Every v->a
 // message is formed from its variable's belief and the edge's current a->v
@@ -82,9 +83,10 @@ __global__ void __launch_bounds__(256, 8) k_beliefs(const DevGraph g, FloodPlanD
 
 // Phase 1, second pass: the rows of several sub-chunks combine their
 // sub-chunk products.  Blocks [0, nb_medium): one thread per medium row;
-// then one warp per hub row.
-__global__ void __launch_bounds__(256) k_row_beliefs(const DevGraph g, FloodPlanDev F)
+// then one block (kFloodSlots threads) per hub row.
+__global__ void __launch_bounds__(kFloodSlots) k_row_beliefs(const DevGraph g, FloodPlanDev F)
 {
+    __shared__ XP s_x[kFloodSlots];
     if (*(volatile const int *)F.done) return;
     const int b = blockIdx.x;
     if (b < F.nb_medium) {
@@ -92,33 +94,36 @@ __global__ void __launch_bounds__(256) k_row_beliefs(const DevGraph g, FloodPlan
         if (w < F.n_medium) belief_medium_item<false>(g, F, w);
         return;
     }
-    const int hr = (b - F.nb_medium) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (hr < F.n_hub_rows) belief_hub_warp<false, 8>(g, F, hr);
+    belief_hub_block<false, 4>(g, F, b - F.nb_medium, s_x);
 }
 
 // ----------------------------------------------------------------------------
 // Phase 2
 // ----------------------------------------------------------------------------
 // Typed factors of at most 32 variables: one lane per message, whole
-// consecutive factors per warp (lanes_warp); the iteration's residual is
-// reduced per block into one of kResSlots words (per graph in a batch).
-// One instantiation per combination of lanes_warp's optional parts.
+// consecutive factors per warp (lanes_warp).  A resident grid: each warp
+// takes warp records w, w + (warps in the grid), ..., keeps its largest
+// residual in a register and reduces once at the end, per block into one of
+// kResSlots words (per graph and per record in a batch).  One instantiation
+// per combination of lanes_warp's optional parts.
 template <int kFeat>
-__global__ void __launch_bounds__(256) k_a2v_lanes(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
+__global__ void __launch_bounds__(256, 8) k_a2v_lanes(const DevGraph g, const FloodPlanDev F, float *__restrict__ a2v,
                                                    float *__restrict__ a2v_vm, IterCtl ctl)
 {
     if (*(volatile const int *)F.done) return;
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    float dd = 0.f;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    float dmax = 0.f;
     unsigned long long ng = 0;
-    int graph = -1;
-    if (w < F.n_twarps) lanes_warp<false, kFeat>(g, F, a2v, a2v_vm, w, dd, ng, graph);  // warp-uniform
-    if (ng) atomicAdd(ctl.guards, ng);
-    if constexpr ((kFeat & kFeatBatch) != 0) {
-        batch_residual(F, graph, dd);
-        return;
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < F.n_twarps; w += nw) {  // warp-uniform
+        float dd = 0.f;
+        int graph = -1;
+        lanes_warp<false, kFeat>(g, F, a2v, a2v_vm, w, dd, ng, graph);
+        if constexpr ((kFeat & kFeatBatch) != 0) batch_residual(F, graph, dd);
+        else dmax = fmaxf(dmax, dd);
     }
-    const float bm = block_max(dd);
+    if (ng) atomicAdd(ctl.guards, ng);
+    if constexpr ((kFeat & kFeatBatch) != 0) return;
+    const float bm = block_max(dmax);
     if (threadIdx.x == 0 && bm > 0.f) max_bits(ctl.res + (blockIdx.x % kResSlots), __float_as_uint(bm));
 }
 
@@ -311,8 +316,8 @@ void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a
 {
     const int nb1 = (P.n_subs + P.sub_threads - 1) / P.sub_threads + P.nb_vars;
     if (nb1 > 0) k_beliefs<<<nb1, 256, 0, s>>>(g, P, a2v_vm);
-    const int nb2 = P.nb_medium + (P.n_hub_rows + 7) / 8;
-    if (nb2 > 0) k_row_beliefs<<<nb2, 256, 0, s>>>(g, P);
+    const int nb2 = P.nb_medium + P.n_hub_rows;
+    if (nb2 > 0) k_row_beliefs<<<nb2, kFloodSlots, 0, s>>>(g, P);
     if (P.n_wide > 0) k_wide_v2a<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v);
     if (P.n_twarps > 0) {
         const int feat = (P.batch.n_graphs > 0 ? kFeatBatch : 0) | (P.elevel ? kFeatLevel : 0) | (P.dres ? kFeatDres : 0);
@@ -327,7 +332,9 @@ void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a
         case 6: k = k_a2v_lanes<6>; break;
         default: k = k_a2v_lanes<7>; break;
         }
-        k<<<(P.n_twarps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
+        // one resident grid: 8 blocks of 256 threads per SM (32 registers a thread)
+        const int nb = (int)std::min<int64_t>((P.n_twarps + 7) / 8, 8 * (int64_t)num_sms());
+        k<<<nb, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
     }
     if (P.n_warps > 0) k_a2v_fused<<<(P.n_warps + 7) / 8, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);
     if (P.n_wide > 0) k_a2v_wide<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v, a2v_vm, ctl);

@@ -18,6 +18,8 @@ constexpr int kFloodSmallMax = 8;      // rows up to this degree: one thread eac
 constexpr int kFloodSub = 32;          // the grouping unit of a longer row's product
 constexpr int kFloodMediumMax = 256;   // rows up to this degree may combine in one thread
 static_assert(kFloodMediumMax <= 8 * kFloodSub, "a medium row has at most 8 sub-chunks");
+constexpr int kFloodSlots = 256;       // slots of a longer row's product (one block's threads)
+static_assert(kFloodSlots >= 64 && (kFloodSlots & (kFloodSlots - 1)) == 0, "a power of two above a warp");
 constexpr int kFloodChunkUnit = 256;   // FBP_OPT_FLOOD_CHUNK is a multiple of this many entries
 constexpr int kFloodHubChunk = 8192;   // entries per block of the sub-chunk pass (default)
 static_assert(kFloodHubChunk % kFloodChunkUnit == 0 && kFloodChunkUnit % kFloodSub == 0, "whole sub-chunks");
@@ -27,7 +29,7 @@ struct FloodPlanDev {
     // phase 1 (beliefs, variable-major): every variable of degree <= 8 one
     // thread (nb_vars blocks stepping through the variables); every longer row in 32-entry
     // sub-chunks, one thread each (a row of one sub-chunk writes its belief
-    // there); then one thread per medium row (2..8 sub-chunks) or one warp per
+    // there); then one thread per medium row (2..8 sub-chunks) or one block per
     // hub row combines the sub-chunk products
     int32_t nb_vars = 0;
     int32_t n_subs = 0;

@@ -319,7 +319,7 @@ __device__ __forceinline__ void belief_var_loop(const DevGraph &g, const FloodPl
     }
 }
 
-// Medium row w (2..8 sub-chunks): the butterfly over 32 slots of which slots
+// Medium row w (2..8 sub-chunks): the butterfly over the slots of which slots
 // 0..ns-1 hold sub-chunk products (the others the identity), evaluated by one
 // thread: slot 0 ends with ((P0 P4)(P2 P6)) ((P1 P5)(P3 P7)); a product with
 // the identity is the value itself, so missing sub-chunks are skipped.
@@ -349,35 +349,45 @@ __device__ __forceinline__ void belief_medium_item(const DevGraph &g, const Floo
     F.belief[row.x] = belief_pack(t);
 }
 
-// Hub row hr, one whole warp: lane j combines sub-chunks j, j+32, ... in
-// order, then the xor butterfly.  The largest rows have thousands of
-// sub-chunks, so each lane keeps the next kD of its products in flight while
-// it combines (the chain, not the arithmetic, sets this kernel's time; kD
-// only trades registers for that).
+// Hub row hr, one whole block of kFloodSlots threads: thread j combines
+// sub-chunks j, j + kFloodSlots, ... in order, keeping the next kD of them in
+// flight (the chain, not the arithmetic, sets the time; kD only trades
+// registers for that), then the xor butterfly over the slots: j with j^128,
+// j^64, j^32 through shared memory s_x (kFloodSlots records), the rest by
+// shuffle in warp 0.  Every thread of the block calls it with the same hr.
 template <bool kC, int kD>
-__device__ __forceinline__ void belief_hub_warp(const DevGraph &g, const FloodPlanDev &F, int hr)
+__device__ __forceinline__ void belief_hub_block(const DevGraph &g, const FloodPlanDev &F, int hr, XP *s_x)
 {
-    const int lane = threadIdx.x & 31;
+    const int j0 = threadIdx.x;
     const int4 row = __ldg(F.hub_row + hr);  // {variable, first agg slot, sub-chunks, 0}
-    if (var_frozen(F, row.x)) return;        // warp-uniform
+    if (var_frozen(F, row.x)) return;        // block-uniform
     const XP *P = F.agg + row.y;
     const int n = row.z;
     XP buf[kD];
 #pragma unroll
-    for (int d = 0; d < kD; ++d) buf[d] = lane + 32 * d < n ? ldx<kC>(P + lane + 32 * d) : xp_one();
+    for (int d = 0; d < kD; ++d) buf[d] = j0 + kFloodSlots * d < n ? ldx<kC>(P + j0 + kFloodSlots * d) : xp_one();
     XP t = xp_one();
-    for (int base = 0; base < n; base += 32 * kD) {  // warp-uniform
+    for (int base = 0; base < n; base += kFloodSlots * kD) {  // block-uniform
 #pragma unroll
         for (int d = 0; d < kD; ++d) {
-            const int j = base + 32 * d + lane, jn = j + 32 * kD;
+            const int j = base + kFloodSlots * d + j0, jn = j + kFloodSlots * kD;
             if (j < n) t = xcombine(t, buf[d]);
             if (jn < n) buf[d] = ldx<kC>(P + jn);
         }
     }
-    t = warp_product(t);
-    if (lane == 0) {
-        xmul(t, __ldg(g.phi + row.x));
-        F.belief[row.x] = belief_pack(t);
+#pragma unroll
+    for (int k = kFloodSlots / 2; k >= 32; k >>= 1) {
+        s_x[j0] = t;
+        __syncthreads();
+        if (j0 < k) t = xcombine(t, s_x[j0 + k]);
+        __syncthreads();
+    }
+    if (j0 < 32) {
+        t = warp_product(t);
+        if (j0 == 0) {
+            xmul(t, __ldg(g.phi + row.x));
+            F.belief[row.x] = belief_pack(t);
+        }
     }
 }
 
@@ -510,7 +520,7 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
         const float r = enc_fast(mu, gd);
         ng += gd;
         dd = delta_p1_fast(r, old);
-        __stcs(a2v + e, r);
+        a2v[e] = r;  // a plain store: the next iteration's phase 2 reads it back, and L2 may keep it
         a2v_vm[slot] = r;
         if constexpr ((kFeat & kFeatDres) != 0) F.dres[e] = dd;
     }

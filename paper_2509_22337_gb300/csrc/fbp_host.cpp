@@ -288,7 +288,7 @@ int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<
     F.n_subs = (int32_t)subs.size();
     F.sub_threads = std::max(32, std::min(256, g->flood_chunk / kFloodSub));
     F.n_medium = (int32_t)medium.size();
-    F.nb_medium = (F.n_medium + 255) / 256;
+    F.nb_medium = (F.n_medium + kFloodSlots - 1) / kFloodSlots;
     F.n_hub_rows = (int32_t)hub_row.size();
     int32_t *d_vpos = nullptr;
     int4 *d_subs = nullptr, *d_medium = nullptr, *d_hub_row = nullptr;

@@ -224,8 +224,8 @@ def pair_model_bytes_per_pass(g):
 # Sources each profiled kernel is built from: a DRAM traffic figure taken by
 # ncu is reported only while these files are unchanged.
 KERNEL_SOURCES = {
-    "k_engine": ["fbp_engine.cu", "fbp_msg.cuh", "fbp_internal.h"],
-    "flood": ["fbp_flood.cu", "fbp_flood.h", "fbp_msg.cuh", "fbp_internal.h"],
+    "k_engine": ["fbp_engine.cu", "fbp_msg.cuh", "fbp_internal.h", "fbp_flood_dev.cuh", "fbp_flood.h"],
+    "flood": ["fbp_flood.cu", "fbp_flood.h", "fbp_flood_dev.cuh", "fbp_msg.cuh", "fbp_internal.h"],
 }
 
 

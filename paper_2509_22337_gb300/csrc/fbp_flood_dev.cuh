@@ -490,6 +490,7 @@ __device__ __forceinline__ void lanes_warp(const DevGraph &g, const FloodPlanDev
     if (eq) my = P2{1.f, 1.f};
     float X = 1.f, Y = 1.f, D = 0.f;
     const int span = __reduce_max_sync(0xffffffffu, valid ? np : 0);
+#pragma unroll 2
     for (int j = 0; j < span; ++j) {
         const int src = (first + j) & 31;
         const float m0 = __shfl_sync(0xffffffffu, me.m0, src), m1 = __shfl_sync(0xffffffffu, me.m1, src);

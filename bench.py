@@ -47,6 +47,10 @@ WORKLOADS = {
                          "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); "
                          "RESIDUAL (classes and Algorithm 2 levels built on the device every iteration) to max "
                          "change < 1e-6 or 500 iterations"),
+    "bingo1m_seqfix": ("bingo", "SEQFIX", 2, 0.0,
+                       "BINGO-shaped cyclic derivation graph: 1M tuples, 2M NOISY_AND rules (+3M vars); SEQFIX "
+                       "(one message at a time in edge order, run as Algorithm 2's levels), exactly 2 sweeps, by "
+                       "the belief-form sequential engine (FBP_OPT_ENGINE = 3)"),
     "tiny": ("tiny", "PARALL", 50, 0.0, "tiny derivation DAG, PARALL, exactly 50 iterations"),
     "generic200k": ("generic", "TOPO_FB", 100, 1e-6,
                     "SmartFL-200k structure with every factor generic: random term lists (1-6 terms, "
@@ -72,7 +76,13 @@ WORKLOADS = {
 # variable, and BINGO's hub variables carry ~1e5 edges (one RESIDUAL iteration
 # of the 1M-tuple graph took 562 s on one core).  The CPU sample then runs the
 # same generator at a smaller scale, and says so.
+# graph options a workload sets after creating its graph handle (option id: value)
+WORKLOAD_OPTIONS = {"bingo1m_seqfix": {3: 3}}  # FBP_OPT_ENGINE: the belief-form sequential engine
+
 ORACLE_SAMPLE_GRAPHS = {
+    "bingo1m_seqfix": (dict(n_tuples=50_000),
+                       "the same generator at 1/20 scale (50k tuples; the oracle's cost per update grows with the "
+                       "degrees of the factor's variables, so this overstates its full-size rate)"),
     "bingo1m_residual": (dict(n_tuples=100_000),
                          "the same generator at 1/10 scale (100k tuples; this overstates the oracle's full-size "
                          "rate, as its cost per edge grows with hub degree)"),
@@ -226,6 +236,7 @@ def pair_model_bytes_per_pass(g):
 KERNEL_SOURCES = {
     "k_engine": ["fbp_engine.cu", "fbp_msg.cuh", "fbp_internal.h", "fbp_flood_dev.cuh", "fbp_flood.h"],
     "flood": ["fbp_flood.cu", "fbp_flood.h", "fbp_flood_dev.cuh", "fbp_msg.cuh", "fbp_internal.h"],
+    "k_seq": ["fbp_seq.cu", "fbp_flood.h", "fbp_flood_dev.cuh", "fbp_msg.cuh", "fbp_internal.h"],
 }
 
 
@@ -734,6 +745,8 @@ def run_gpu(args):
     g = make_graph(args.workload)
     stream = torch.cuda.current_stream()
     G = F.Graph(g, strategy, stream=stream)
+    for k, v in WORKLOAD_OPTIONS.get(args.workload, {}).items():
+        G.set_option(k, v)
     p_out = torch.empty(max(g.n_vars, 1), dtype=torch.float32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
@@ -795,6 +808,12 @@ def run_gpu(args):
         launches_per_step = max(sweeps, 1)
         bytes_per_launch = pair_model_bytes_per_pass(g)
         layout_bytes = algorithmic_bytes_flood(g)
+    elif WORKLOAD_OPTIONS.get(args.workload, {}).get(3) == 3:
+        kname = "k_seq_belief (belief-form sequential engine: one block, one launch per run)"
+        kkey = "k_seq"
+        halves = 2 if strategy == "TOPO_FB" else 1
+        bytes_per_launch = pair_model_bytes_per_pass(g) * halves * sweeps / launches_per_step
+        layout_bytes = bytes_per_launch
     else:
         kname = "k_engine (persistent level engine, one launch per run)"
         kkey = "k_engine"
@@ -828,6 +847,8 @@ def run_gpu(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             H = F.Graph(g, strategy, stream=stream)
+            for k, v in WORKLOAD_OPTIONS.get(args.workload, {}).items():
+                H.set_option(k, v)
             H.run(max_iters, tol)
             host_p[:] = H.marginals()
             sth = H.stats()

@@ -209,7 +209,15 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  *                      engine with a grid barrier between levels; 2: the
  *                      persistent engine in dataflow form (a lane waits only
  *                      for the messages it reads from earlier levels; same
- *                      results); 0: one launch per level (reference path).
+ *                      results); 0: one launch per level (reference path);
+ *                      3: the belief-form sequential engine for graphs with
+ *                      high-degree variables (each variable's belief is kept
+ *                      current level by level and v->a = belief / own
+ *                      message, so a message costs its factor's size instead
+ *                      of its variables' degrees; the same schedule and
+ *                      iteration count, FP32 products grouped as in the
+ *                      flooding kernels, so results differ from 0-2 by
+ *                      rounding).  Batches always use the level engine.
  * FBP_OPT_ENGINE_CLUSTER 0 (default): automatic; 1: never run the engine as
  *                      one thread-block cluster; 8 or 16: always, with that
  *                      cluster size.
@@ -218,8 +226,9 @@ int fbp_get_stats(const fbp_graph *g, fbp_stats *out);
  * FBP_OPT_FLOOD_CHUNK  flooding: entries of such a variable per block
  *                      (a multiple of 256 in 256..65536, default 1024).
  *                      Neither split option changes a result: a long row's
- *                      product is grouped in 256-entry sub-chunks whichever
- *                      kernel carries it, so messages are bit-identical.
+ *                      product is grouped one fixed way (32-entry sub-chunks
+ *                      dealt to 256 slots, then a butterfly) whichever kernel
+ *                      carries it, so messages are bit-identical.
  * FBP_OPT_ENGINE_FUSE_LANES  level fusion of the grid engine (0..256,
  *                      default 0 = off): a level of at most this many lanes
  *                      (one lane per variable of each factor it touches) and

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libfbp.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fbp_kernels.cu", "fbp_engine.cu", "fbp_flood.cu", "fbp_host.cpp", "fbp_sched.cpp", "fbp_batch.cpp", "fbp_serve.cpp",
-           "fbp_fixed.cu", "fbp_residual.cu"]
+           "fbp_fixed.cu", "fbp_residual.cu", "fbp_seq.cu"]
 
 
 def nvcc() -> str:

@@ -311,13 +311,19 @@ __global__ void k_flood_check(unsigned *slots, unsigned *hist, float tol, int *c
     }
 }
 
-// Phase 1 and phase 2 of one iteration (or one RESIDUAL level).
-void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a2v_vm, IterCtl ctl, cudaStream_t s)
+// Phase 1 of an iteration.
+void beliefs_phase(const DevGraph &g, const FloodPlanDev &P, const float *a2v_vm, cudaStream_t s)
 {
     const int nb1 = (P.n_subs + P.sub_threads - 1) / P.sub_threads + P.nb_vars;
     if (nb1 > 0) k_beliefs<<<nb1, 256, 0, s>>>(g, P, a2v_vm);
     const int nb2 = P.nb_medium + P.n_hub_rows;
     if (nb2 > 0) k_row_beliefs<<<nb2, kFloodSlots, 0, s>>>(g, P);
+}
+
+// Phase 1 and phase 2 of one iteration (or one RESIDUAL level).
+void flood_phases(const DevGraph &g, const FloodPlanDev &P, float *a2v, float *a2v_vm, IterCtl ctl, cudaStream_t s)
+{
+    beliefs_phase(g, P, a2v_vm, s);
     if (P.n_wide > 0) k_wide_v2a<<<(P.n_wide + 255) / 256, 256, 0, s>>>(g, P, a2v);
     if (P.n_twarps > 0) {
         const int feat = (P.batch.n_graphs > 0 ? kFeatBatch : 0) | (P.elevel ? kFeatLevel : 0) | (P.dres ? kFeatDres : 0);
@@ -388,6 +394,11 @@ cudaError_t flood_capture(const DevGraph &g, const FloodPlanDev &F, float *a2v, 
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     return e;
+}
+
+void flood_beliefs(const DevGraph &g, const FloodPlanDev &F, const float *a2v_vm, cudaStream_t s)
+{
+    beliefs_phase(g, F, a2v_vm, s);
 }
 
 int flood_launches(const DevGraph &g, const FloodPlanDev &F)

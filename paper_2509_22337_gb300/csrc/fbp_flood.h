@@ -120,6 +120,9 @@ void flood_iteration(const DevGraph &g, const FloodPlanDev &F, float *a2v, float
 // then the level's a->v messages.  No convergence check.
 void flood_level(const DevGraph &g, const FloodPlanDev &F, float *a2v, float *a2v_vm, IterCtl ctl, int *done,
                  cudaStream_t s);
+// Phase 1 alone: every variable's belief record from a2v_vm (F.done must
+// point to a word that reads 0).
+void flood_beliefs(const DevGraph &g, const FloodPlanDev &F, const float *a2v_vm, cudaStream_t s);
 // End of a device-scheduled RESIDUAL iteration: the check of flood_iteration.
 void flood_check(IterCtl ctl, float tol, unsigned *hist, int *done, cudaStream_t s);
 // A CUDA graph of `iters` consecutive flood_iterations (captured on a private

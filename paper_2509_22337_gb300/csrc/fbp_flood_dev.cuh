@@ -324,9 +324,9 @@ __device__ __forceinline__ void belief_var_loop(const DevGraph &g, const FloodPl
 // thread: slot 0 ends with ((P0 P4)(P2 P6)) ((P1 P5)(P3 P7)); a product with
 // the identity is the value itself, so missing sub-chunks are skipped.
 template <bool kC>
-__device__ __forceinline__ void belief_medium_item(const DevGraph &g, const FloodPlanDev &F, int w)
+__device__ __forceinline__ void belief_medium_row(const DevGraph &g, const FloodPlanDev &F, const int4 row)
 {
-    const int4 row = __ldg(F.medium + w);  // {variable, first agg slot, sub-chunks (2..8), 0}
+    // row = {variable, first agg slot, sub-chunks (2..8), 0}
     if (var_frozen(F, row.x)) return;
     const XP *P = F.agg + row.y;
     const int ns = row.z;
@@ -347,6 +347,12 @@ __device__ __forceinline__ void belief_medium_item(const DevGraph &g, const Floo
     t = xcombine(t, u);
     xmul(t, __ldg(g.phi + row.x));
     F.belief[row.x] = belief_pack(t);
+}
+
+template <bool kC>
+__device__ __forceinline__ void belief_medium_item(const DevGraph &g, const FloodPlanDev &F, int w)
+{
+    belief_medium_row<kC>(g, F, __ldg(F.medium + w));
 }
 
 // Hub row hr, one whole block of kFloodSlots threads: thread j combines

@@ -28,6 +28,21 @@ struct LevelSet {                    // one level list (one half of TOPO_FB)
     int64_t n_lanes = 0;
 };
 
+// One level list of the belief-form sequential engine (FBP_OPT_ENGINE = 3):
+// per level, its edges and the work that keeps the beliefs current after
+// the level's writes (each list without repeats).
+struct SeqHalf {
+    int32_t n_levels = 0;
+    int32_t max_level = 0;           // edges of the widest level
+    int32_t *lp = nullptr;           // [n_levels + 1] level starts in le
+    int32_t *le = nullptr;           // level edges
+    int4 *dp = nullptr;              // [n_levels + 1] starts of {short rows, sub-chunks, medium rows, hub rows}
+    int32_t *dv = nullptr;           // variables of degree <= 8 to recompute
+    int32_t *dk = nullptr;           // sub-chunks (indices of the flooding plan's list) to recompute
+    int32_t *dm = nullptr;           // medium rows to recombine
+    int32_t *dh = nullptr;           // hub rows to recombine
+};
+
 struct fbp_graph {
     HostCSR h;                        // host CSR + transpose (also used by scheduling)
     std::vector<float> prior;
@@ -63,9 +78,16 @@ struct fbp_graph {
     int engine_fuse = 0;              // level fusion: narrow levels (<= this many lanes) in one block (0: off)
     int engine_solo = 128;            // whole run in one block when levels average <= this many lanes
     int use_engine = 1;
-    // flooding plan
+    // flooding plan, with host copies of its row lists (the sequential
+    // engine's plan indexes them)
     FloodPlanDev flood;
     bool flood_ready = false;
+    std::vector<int4> flood_subs_h, flood_medium_h, flood_hub_h;
+    // belief-form sequential engine: plan (built for the current flooding
+    // plan and schedule; empty when stale) and the staging of wide levels
+    std::vector<SeqHalf> seq;
+    float *seq_tmp = nullptr;
+    int64_t seq_tmp_cap = 0;
     // captured chunk of flooding iterations and what it was captured for
     cudaGraphExec_t flood_exec = nullptr;
     int flood_exec_iters = 0;
@@ -116,6 +138,10 @@ int upload(fbp_graph *g, T **p, const T *src, size_t n)
 }
 void free_levels_one(fbp_graph *g, LevelSet &ls);
 void free_levels(fbp_graph *g);
+// The belief-form sequential engine (csrc/fbp_seq.cu): drop its plan (after
+// the schedule or the flooding plan changed), and run a static schedule.
+void free_seq(fbp_graph *g);
+int run_seq(fbp_graph *g, int32_t max_iters, double tol, int32_t *iters_out, double *residual_out);
 // Upload a level list's engine plan: `packed` when given (pack_levels of the
 // same list), else packed here.
 int upload_levels(fbp_graph *g, LevelSet &ls, const fbp::LevelPack *packed = nullptr);
@@ -129,6 +155,7 @@ int engine_check(fbp_graph *g);
 int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *fvars, const uint8_t *ftype,
                      const float *fparam, const float *prior, const int8_t *evidence);
 int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_out, double *residual_out);
+double residual_at(fbp_graph *g, int32_t it);
 // The graph's captured chunk of `iters` flooding iterations under plan F and
 // tolerance tol (captured again when any of them, the message buffer or the
 // residual words changed).

@@ -122,6 +122,7 @@ void free_levels(fbp_graph *g)
 {
     for (auto &ls : g->halves) free_levels_one(g, ls);
     g->halves.clear();
+    free_seq(g);  // built from these level lists
 }
 
 // Engine plan of one level list.  Per level, the factors the level touches
@@ -186,6 +187,7 @@ int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<
 {
     const HostCSR &h = g->h;
     flood_exec_drop(g);
+    free_seq(g);  // indexes this plan's lists
     if (g->flood_ready) {  // a rebuild after retuning
         dfree(g, (void *)g->flood.subs);
         dfree(g, (void *)g->flood.medium);
@@ -322,6 +324,9 @@ int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<
     F.wide = d_wide;
     F.wide_v2a = d_wide_v2a;
     g->flood = F;
+    g->flood_subs_h = std::move(subs);
+    g->flood_medium_h = std::move(medium);
+    g->flood_hub_h = std::move(hub_row);
     g->flood_ready = true;
     return FBP_OK;
 }
@@ -968,9 +973,11 @@ extern "C" int fbp_run(fbp_graph *g, int32_t max_iters, double tol, int32_t *ite
     if (g->strategy == FBP_RESIDUAL)
         return g->residual_device ? fbp_run_residual_device(g, max_iters, tol, iters_out, residual_out)
                                   : fbp_run_residual(g, max_iters, tol, iters_out, residual_out);
-    if (g->strategy != FBP_PARALL)
+    if (g->strategy != FBP_PARALL) {
+        if (g->use_engine == 3) return run_seq(g, max_iters, tol, iters_out, residual_out);
         return g->use_engine ? run_engine(g, max_iters, tol, iters_out, residual_out)
                              : run_per_level(g, max_iters, tol, iters_out, residual_out);
+    }
     // flooding: a captured chunk of kFloodChunk iterations is replayed in
     // growing batches; the device counts iterations, marks the run done at
     // convergence or at the limit, and later kernels return at once
@@ -1226,7 +1233,7 @@ extern "C" int fbp_set_option(fbp_graph *g, int32_t option, int64_t value)
         g->residual_device = value != 0;
         return FBP_OK;
     case FBP_OPT_ENGINE:
-        if (value < 0 || value > 2) return fail(FBP_ERR_INVALID_ARG, "FBP_OPT_ENGINE must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(FBP_ERR_INVALID_ARG, "FBP_OPT_ENGINE must be 0, 1, 2 or 3");
         g->use_engine = (int)value;
         return FBP_OK;
     case FBP_OPT_FLOOD_HUB_MIN:

@@ -121,8 +121,14 @@ __device__ __forceinline__ void seq_sub_warp(const SeqArgs &S, const int4 sc)
     const int lane = threadIdx.x & 31;
     // sc = {variable, begin, end, agg slot or -1}
     const float x = sc.y + lane < sc.z ? __ldcg(S.a2v_vm + sc.y + lane) : 1.f;
+    float xs[kFloodSub];  // every shuffle first, so the multiply chain does not wait on them
+#pragma unroll
+    for (int j = 0; j < kFloodSub; ++j) xs[j] = __shfl_sync(0xffffffffu, x, j);
     XP t = xp_one();
-    for (int j = 0; j < sc.z - sc.y; ++j) xmul(t, __shfl_sync(0xffffffffu, x, j));
+    const int len = sc.z - sc.y;
+#pragma unroll
+    for (int j = 0; j < kFloodSub; ++j)
+        if (j < len) xmul(t, xs[j]);
     if (lane != 0) return;
     if (sc.w >= 0) {
         S.F.agg[sc.w] = t;
@@ -142,7 +148,7 @@ constexpr int kSeqWarps = kFloodSlots / 32;
 constexpr int kSeqStage = 1024;  // new messages of a level staged in shared memory
 
 // The whole run in one block of kFloodSlots threads.
-__global__ void __launch_bounds__(kFloodSlots) k_seq_belief(const SeqArgs S)
+__global__ void __launch_bounds__(kFloodSlots, 1) k_seq_belief(const SeqArgs S)
 {
     __shared__ XP s_x[kFloodSlots];
     __shared__ float s_r[kSeqStage];

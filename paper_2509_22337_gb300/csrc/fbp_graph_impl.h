@@ -30,17 +30,18 @@ struct LevelSet {                    // one level list (one half of TOPO_FB)
 
 // One level list of the belief-form sequential engine (FBP_OPT_ENGINE = 3):
 // per level, its edges and the work that keeps the beliefs current after
-// the level's writes (each list without repeats).
+// the level's writes.
 struct SeqHalf {
     int32_t n_levels = 0;
     int32_t max_level = 0;           // edges of the widest level
     int32_t *lp = nullptr;           // [n_levels + 1] level starts in le
     int32_t *le = nullptr;           // level edges
-    int4 *dp = nullptr;              // [n_levels + 1] starts of {short rows, sub-chunks, medium rows, hub rows}
-    int32_t *dv = nullptr;           // variables of degree <= 8 to recompute
-    int32_t *dk = nullptr;           // sub-chunks (indices of the flooding plan's list) to recompute
-    int32_t *dm = nullptr;           // medium rows to recombine
-    int32_t *dh = nullptr;           // hub rows to recombine
+    int4 *dp = nullptr;              // [n_levels + 1] starts of {short items, sub-chunk items, whole medium rows, whole hub rows}
+    int4 *ds = nullptr;              // short rows to recompute {variable, patch begin, patch end, 0}
+    int4 *dk = nullptr;              // sub-chunks to recompute {sub-chunk, patch begin, patch end, finish}
+    int32_t *dm = nullptr;           // medium rows with several touched sub-chunks
+    int32_t *dh = nullptr;           // hub rows with several touched sub-chunks
+    int2 *pt = nullptr;              // patches {position in the row or sub-chunk, index in the level}
 };
 
 struct fbp_graph {
@@ -88,6 +89,7 @@ struct fbp_graph {
     std::vector<SeqHalf> seq;
     float *seq_tmp = nullptr;
     int64_t seq_tmp_cap = 0;
+    fbp::XP *seq_tree = nullptr;      // butterfly nodes of every hub row
     // captured chunk of flooding iterations and what it was captured for
     cudaGraphExec_t flood_exec = nullptr;
     int flood_exec_iters = 0;

@@ -38,7 +38,9 @@ extern "C" {
  * fbp_get_stats figures except kernel_launches: this call always runs the
  * persistent level engine in one launch (kernel_launches = 1), also when
  * FBP_OPT_ENGINE = 0 asks fbp_run for one launch per level, which computes
- * the same messages.
+ * the same messages.  FBP_OPT_ENGINE = 3 (the belief-form sequential engine,
+ * which rounds differently) is not honoured here: the comparison holds
+ * against fbp_run with FBP_OPT_ENGINE 0, 1 or 2.
  *
  * Memory: allocates no device memory (no cudaMalloc, no call of the graph's
  * allocator, no library routine that allocates).  The per-run scratch -- the

@@ -212,14 +212,16 @@ def test_smartfl_200k_topo_fb_full_size(fbp):
     assert_parity(a, b, "smartfl200k TOPO_FB")
 
 
-def test_bingo_1m_sampled_one_step(fbp):
+@pytest.mark.parametrize("warm", [5, 100])
+def test_bingo_1m_sampled_one_step(fbp, warm):
     """BINGO-shaped 1M-tuple graph in the bench's launch configuration: after
-    5 GPU flooding iterations, one more GPU iteration is compared message by
-    message (a sample of 2,000 edges) with the oracle's synchronous update from
-    the same exported state."""
+    `warm` GPU flooding iterations (by 100 the messages span some 17 decades,
+    as in the benched 500-iteration run), one more GPU iteration is compared
+    message by message (a sample of 2,000 edges) with the oracle's synchronous
+    update from the same exported state."""
     g = gen.bingo()
     G = fbp.Graph(g, "PARALL")
-    G.run(5, 0.0)
+    G.run(warm, 0.0)
     s5 = G.messages().astype(np.float64)
     G.run(1, 0.0)
     s6 = G.messages().astype(np.float64)

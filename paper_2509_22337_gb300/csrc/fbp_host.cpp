@@ -471,7 +471,9 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
     g->evidence.assign(evidence ? evidence : nullptr, evidence ? evidence + n_vars : nullptr);
     if (!evidence) g->evidence.assign(n_vars, (int8_t)-1);
     g->phi.resize(n_vars);
-    for (int32_t v = 0; v < n_vars; ++v) g->phi[v] = phi_of(g->prior[v], g->evidence[v]);
+    parallel_for(n_vars, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t v = b; v < e; ++v) g->phi[v] = phi_of(g->prior[v], g->evidence[v]);
+    });
 
     int32_t *fptr32 = nullptr, *fvars = nullptr, *efac = nullptr, *vptr = nullptr, *vedge = nullptr;
     uint8_t *ftype = nullptr;

@@ -2,6 +2,7 @@
 #include "fbp_sched.h"
 
 #include <algorithm>
+#include <memory>
 #include <cstring>
 #include <limits>
 #include <numeric>
@@ -15,21 +16,61 @@ void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *
     h.nv = nv;
     h.na = na;
     h.ne = (int32_t)fptr[na];
+    const int64_t ne = h.ne;
+    const int threads = host_threads();
     h.fptr.assign(fptr, fptr + na + 1);
-    h.fvars.assign(fvars, fvars + h.ne);
     h.ftype.assign(ftype, ftype + na);
     h.fparam.assign(fparam, fparam + na);
-    h.efac.resize(h.ne);
-    h.vptr.assign((size_t)nv + 1, 0);
-    for (int32_t a = 0; a < na; ++a)
-        for (int64_t e = fptr[a]; e < fptr[a + 1]; ++e) {
-            h.efac[e] = a;
-            h.vptr[fvars[e] + 1]++;
+    h.fvars.resize(ne);
+    h.efac.resize(ne);
+    parallel_for(na, threads, 1 << 14, [&](int64_t b, int64_t e) {
+        for (int64_t a = b; a < e; ++a)
+            for (int64_t k = fptr[a]; k < fptr[a + 1]; ++k) {
+                h.fvars[k] = fvars[k];
+                h.efac[k] = (int32_t)a;
+            }
+    });
+    // The transpose, a stable counting sort of the edges by variable over P
+    // contiguous parts of the edge range: each part counts its variables; a
+    // variable's row takes part 0's edges, then part 1's, ...; each part
+    // scatters its edges in order, so every row lists its edges in
+    // ascending id, as the one-part (serial) sort does.  The parts' counters
+    // take P * nv words, so P is bounded by a budget of 2^26 words.
+    const int64_t parts = std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)threads, ne / 65536, (int64_t(1) << 26) / std::max<int64_t>(nv, 1)}));
+    const int64_t step = (ne + parts - 1) / parts;
+    std::vector<std::unique_ptr<int32_t[]>> cnt(parts);
+    for (auto &c : cnt) c.reset(new int32_t[std::max<int64_t>(nv, 1)]);
+    parallel_for(parts, (int)parts, 1, [&](int64_t pb, int64_t pe) {
+        for (int64_t k = pb; k < pe; ++k) {
+            int32_t *c = cnt[k].get();
+            std::fill(c, c + nv, 0);
+            for (int64_t e = k * step, end = std::min(ne, (k + 1) * step); e < end; ++e) c[fvars[e]]++;
         }
+    });
+    h.vptr.assign((size_t)nv + 1, 0);
+    parallel_for(nv, threads, 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t v = b; v < e; ++v) {
+            int32_t sum = 0;
+            for (int64_t k = 0; k < parts; ++k) {
+                const int32_t c = cnt[k][v];
+                cnt[k][v] = sum;  // part k's first slot within the row
+                sum += c;
+            }
+            h.vptr[v + 1] = sum;
+        }
+    });
     for (int32_t v = 0; v < nv; ++v) h.vptr[v + 1] += h.vptr[v];
-    h.vedge.resize(h.ne);
-    std::vector<int32_t> fill(h.vptr.begin(), h.vptr.end() - 1);
-    for (int32_t e = 0; e < h.ne; ++e) h.vedge[fill[fvars[e]]++] = e;  // ascending edge id per row
+    h.vedge.resize(ne);
+    parallel_for(parts, (int)parts, 1, [&](int64_t pb, int64_t pe) {
+        for (int64_t k = pb; k < pe; ++k) {
+            int32_t *c = cnt[k].get();
+            for (int64_t e = k * step, end = std::min(ne, (k + 1) * step); e < end; ++e) {
+                const int32_t v = fvars[e];
+                h.vedge[h.vptr[v] + c[v]++] = (int32_t)e;
+            }
+        }
+    });
 }
 
 // TOPO: depth of every variable over the "premise -> output" relation of the

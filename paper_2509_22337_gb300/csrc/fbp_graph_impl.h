@@ -60,6 +60,8 @@ struct fbp_graph {
     float *a2v_vm = nullptr;          // flooding: variable-major copy of the a->v messages [E]
     float *pairs = nullptr;           // export/import staging [2E]
     float *p1 = nullptr;              // marginals [V]
+    int32_t *marg_rows = nullptr;     // variables whose rows exceed marginals_row_max() (built at first use)
+    int32_t n_marg_rows = -1;         // -1: not built yet
     // schedule
     int strategy = FBP_PARALL;
     std::vector<LevelSet> halves;     // 1 (static) or 2 (TOPO_FB)
@@ -158,6 +160,13 @@ int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t 
                      const float *fparam, const float *prior, const int8_t *evidence);
 int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_out, double *residual_out);
 double residual_at(fbp_graph *g, int32_t it);
+// Marginals of every variable of g's current messages into device buffer
+// dst on stream s: rows of at most marginals_row_max() entries one thread
+// each, longer rows one block each (csrc/fbp_kernels.cu).
+int marginals_launch(fbp_graph *g, float *dst, cudaStream_t s);
+int marginals_row_max();
+void launch_marginals_long(const DevGraph &g, const float *a2v, float *p1, const int32_t *rows, int32_t n,
+                           cudaStream_t s);
 // The graph's captured chunk of `iters` flooding iterations under plan F and
 // tolerance tol (captured again when any of them, the message buffer or the
 // residual words changed).

@@ -873,6 +873,23 @@ int finish_run(fbp_graph *g, int32_t it, double res, int status, int32_t *iters_
     return status;
 }
 
+int marginals_launch(fbp_graph *g, float *dst, cudaStream_t s)
+{
+    if (g->n_marg_rows < 0) {
+        std::vector<int32_t> rows;
+        const int32_t cap = marginals_row_max();
+        for (int32_t v = 0; v < g->h.nv; ++v)
+            if (g->h.vptr[v + 1] - g->h.vptr[v] > cap) rows.push_back(v);
+        int rc = upload(g, &g->marg_rows, rows.data(), rows.size());
+        if (rc) return rc;
+        g->n_marg_rows = (int32_t)rows.size();
+    }
+    launch_marginals(g->d, g->a2v[g->cur], dst, s);
+    launch_marginals_long(g->d, g->a2v[g->cur], dst, g->marg_rows, g->n_marg_rows, s);
+    CUDA_TRY(cudaGetLastError());
+    return FBP_OK;
+}
+
 double residual_at(fbp_graph *g, int32_t it)
 {
     if (it < 1) return 0.0;
@@ -1281,8 +1298,8 @@ extern "C" int fbp_marginals(const fbp_graph *gc, float *out_p1, int out_is_devi
         if (!g->p1 && dalloc_n(g, &g->p1, (size_t)g->h.nv)) return FBP_ERR_OOM;
         dst = g->p1;
     }
-    launch_marginals(g->d, g->a2v[g->cur], dst, g->stream);
-    CUDA_TRY(cudaGetLastError());
+    int rc = marginals_launch(g, dst, g->stream);
+    if (rc) return rc;
     if (!out_is_device) {
         CUDA_TRY(cudaMemcpyAsync(out_p1, g->p1, sizeof(float) * g->h.nv, cudaMemcpyDeviceToHost, g->stream));
         CUDA_TRY(cudaStreamSynchronize(g->stream));

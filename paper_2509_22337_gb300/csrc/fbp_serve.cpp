@@ -349,9 +349,9 @@ int fbp_server::finish_iterating(Sess &s)
     r.dev_ms = ms;
     if (r.result && s.nv > 0) {
         float *dst = r.result_dev ? r.result : g->p1;
-        launch_marginals(g->d, g->a2v[g->cur], dst, s.stream);
-        stats.kernel_launches += 1;
-        cudaError_t e = cudaGetLastError();
+        if (int rc = marginals_launch(g, dst, s.stream)) return rc;
+        stats.kernel_launches += 1 + (g->n_marg_rows > 0);
+        cudaError_t e = cudaSuccess;
         if (e == cudaSuccess && !r.result_dev)
             e = cudaMemcpyAsync(s.h_stage, g->p1, sizeof(float) * s.nv, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev_chunk, s.stream);

@@ -281,7 +281,7 @@ int build_flood_plan(fbp_graph *g, const std::vector<int4> *ranges, std::vector<
     }
     // slot of each edge in the variable-major copy: the inverse of vedge
     std::vector<int32_t> vpos(h.ne);
-    parallel_for(h.ne, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
+    parallel_for(h.ne, host_threads_all(), 1 << 16, [&](int64_t b, int64_t e) {
         for (int64_t k = b; k < e; ++k) vpos[h.vedge[k]] = (int32_t)k;
     });
     // the short rows' blocks: one resident grid (8 blocks of 256 per SM)
@@ -400,7 +400,7 @@ int check_graph_args(int32_t nv, int32_t na, const int64_t *fptr, const int32_t 
     if (na > 0 && (!ftype || !fparam)) return fail(FBP_ERR_INVALID_ARG, "factor_type/param NULL");
     // the factors in parallel; the lowest-numbered bad factor is reported
     std::atomic<int32_t> first_bad{std::numeric_limits<int32_t>::max()};
-    parallel_for(na, host_threads(), 1 << 15, [&](int64_t b, int64_t e) {
+    parallel_for(na, host_threads_all(), 1 << 15, [&](int64_t b, int64_t e) {
         for (int64_t a = b; a < e && a < first_bad.load(std::memory_order_relaxed); ++a)
             if (check_factor(nv, fptr, fvars, ftype, fparam, (int32_t)a, false)) {
                 int32_t cur = first_bad.load(std::memory_order_relaxed);
@@ -471,7 +471,7 @@ extern "C" int fbp_graph_create(int32_t n_vars, int32_t n_factors, const int64_t
     g->evidence.assign(evidence ? evidence : nullptr, evidence ? evidence + n_vars : nullptr);
     if (!evidence) g->evidence.assign(n_vars, (int8_t)-1);
     g->phi.resize(n_vars);
-    parallel_for(n_vars, host_threads(), 1 << 16, [&](int64_t b, int64_t e) {
+    parallel_for(n_vars, host_threads_all(), 1 << 16, [&](int64_t b, int64_t e) {
         for (int64_t v = b; v < e; ++v) g->phi[v] = phi_of(g->prior[v], g->evidence[v]);
     });
 

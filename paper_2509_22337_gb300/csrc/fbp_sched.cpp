@@ -17,7 +17,7 @@ void build_host_csr(int32_t nv, int32_t na, const int64_t *fptr, const int32_t *
     h.na = na;
     h.ne = (int32_t)fptr[na];
     const int64_t ne = h.ne;
-    const int threads = host_threads();
+    const int threads = host_threads_all();
     h.fptr.assign(fptr, fptr + na + 1);
     h.ftype.assign(ftype, ftype + na);
     h.fparam.assign(fparam, fparam + na);

@@ -24,6 +24,14 @@ inline int host_threads()
     return t;
 }
 
+// Host threads for a pass that runs alone (graph creation, the flooding
+// plan): every hardware thread, at most 32.
+inline int host_threads_all()
+{
+    static const int t = [] { return (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u)); }();
+    return t;
+}
+
 // body(begin, end) over [0, n) in up to `threads` contiguous parts, the first
 // on the calling thread.  Bodies must not throw (they only write into
 // preallocated arrays).

@@ -51,8 +51,8 @@ extern "C" {
 #define FBP_ERR_SCHEDULE    (-4) /* TOPO on a cyclic graph; bad rank array */
 #define FBP_ERR_TIMEOUT     (-5) /* a bounded device wait expired          */
 
-/* ---- factor type codes (Sec. 2.2 and Sec. 3.3; semantics as in the
- *      oracle's readings: NOISY_AND(p): all premises true -> y=1 w.p. p,
+/* ---- factor type codes (Sec. 2.2 and Sec. 3.3), with these semantics:
+ *      NOISY_AND(p): all premises true -> y=1 w.p. p,
  *      any false premise forces y=0; NOISY_IMPLY(p): all premises true ->
  *      y=1 w.p. p, a false premise leaves y free; PRIOR(p): P(y=1) = p) ---- */
 enum {

@@ -25,8 +25,7 @@
 //   C. only where a row had several touched sub-chunks: after a barrier, the
 //      row recombined whole.
 // A message read in step A thus includes every update of the earlier levels,
-// as in the in-place sequential execution of Sec. 4.3 (the oracle's
-// run_levels).  Levels are short (about ten edges on BINGO-1M SEQFIX), so the
+// as in the in-place sequential execution of a schedule's levels (Sec. 4.3).  Levels are short (about ten edges on BINGO-1M SEQFIX), so the
 // whole run is one block of kFloodSlots threads.  Every product is grouped as
 // in the flooding kernels (sub-chunks multiplied in order, 256 slots, the xor
 // butterfly), so a belief kept current here has the bits a flooding phase 1

@@ -15,6 +15,8 @@
 #include "fbp_graph_impl.h"
 
 #include <algorithm>
+#include <thread>
+#include <atomic>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -96,41 +98,113 @@ namespace {
 // every factor / variable.
 int build_union(Part &P, const fbp_graph_desc *graphs, const fbp_allocator *alloc, std::vector<int32_t> &var_graph)
 {
-    std::vector<int64_t> fptr(1, 0);
-    std::vector<int32_t> fvars, fac_graph;
-    std::vector<uint8_t> ftype;
-    std::vector<float> fparam, prior;
-    std::vector<int8_t> ev;
+    // every member's offsets first, then each member copied into place (the
+    // members on every host thread)
+    const size_t m = P.members.size();
     int32_t nv = 0, na = 0;
     int64_t ne = 0;
-    for (size_t k = 0; k < P.members.size(); ++k) {
+    for (size_t k = 0; k < m; ++k) {
         const fbp_graph_desc &d = graphs[P.members[k]];
         P.var_off.push_back(nv);
         P.fac_off.push_back(na);
         P.edge_off.push_back((int32_t)ne);
-        for (int32_t a = 0; a < d.n_factors; ++a) {
-            for (int64_t e = d.factor_ptr[a]; e < d.factor_ptr[a + 1]; ++e) fvars.push_back(d.factor_vars[e] + nv);
-            fptr.push_back(ne + d.factor_ptr[a + 1]);
-            ftype.push_back(d.factor_type[a]);
-            fparam.push_back(d.factor_param[a]);
-            fac_graph.push_back((int32_t)k);
-        }
-        for (int32_t v = 0; v < d.n_vars; ++v) {
-            prior.push_back(d.prior_p1 ? d.prior_p1[v] : std::numeric_limits<float>::quiet_NaN());
-            ev.push_back(d.evidence ? d.evidence[v] : (int8_t)-1);
-            var_graph.push_back((int32_t)k);
-        }
         nv += d.n_vars;
         na += d.n_factors;
         ne += d.factor_ptr[d.n_factors];
         P.max_iters = std::max(P.max_iters, d.max_iters);
     }
     if (ne >= (int64_t)1 << 31) return fail(FBP_ERR_INVALID_ARG, "batch part too large (%lld edges)", (long long)ne);
+    std::vector<int64_t> fptr((size_t)na + 1, 0);
+    std::vector<int32_t> fvars((size_t)ne), fac_graph((size_t)na);
+    std::vector<uint8_t> ftype((size_t)na);
+    std::vector<float> fparam((size_t)na), prior((size_t)nv);
+    std::vector<int8_t> ev((size_t)nv);
+    var_graph.resize((size_t)nv);
+    std::atomic<size_t> next{0};
+    auto work = [&] {
+        for (size_t k; (k = next.fetch_add(1)) < m;) {
+            const fbp_graph_desc &d = graphs[P.members[k]];
+            const int32_t v0 = P.var_off[k], a0 = P.fac_off[k];
+            const int64_t e0 = P.edge_off[k];
+            for (int32_t a = 0; a < d.n_factors; ++a) {
+                for (int64_t e = d.factor_ptr[a]; e < d.factor_ptr[a + 1]; ++e) fvars[e0 + e] = d.factor_vars[e] + v0;
+                fptr[a0 + a + 1] = e0 + d.factor_ptr[a + 1];
+                ftype[a0 + a] = d.factor_type[a];
+                fparam[a0 + a] = d.factor_param[a];
+                fac_graph[a0 + a] = (int32_t)k;
+            }
+            for (int32_t v = 0; v < d.n_vars; ++v) {
+                prior[v0 + v] = d.prior_p1 ? d.prior_p1[v] : std::numeric_limits<float>::quiet_NaN();
+                ev[v0 + v] = d.evidence ? d.evidence[v] : (int8_t)-1;
+                var_graph[v0 + v] = (int32_t)k;
+            }
+        }
+    };
+    const int threads = std::max(1, std::min<int>(host_threads_all(), (int)m));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) {
+        try {
+            pool.emplace_back(work);
+        } catch (...) {  // no thread to be had: the others take its members
+            break;
+        }
+    }
+    work();
+    for (auto &th : pool) th.join();
+
     int rc = fbp_graph_create(nv, na, fptr.data(), fvars.data(), ftype.data(), fparam.data(), prior.data(),
                               ev.data(), alloc, P.stream, &P.g);
     if (rc) return rc;
     P.g->fac_graph = std::move(fac_graph);
     return FBP_OK;
+}
+
+// Every static member's own Algorithm 2 level lists (one per half), built on
+// every host thread, members taken in turn (their sizes differ); the
+// callers concatenate them in member order, so the result is the one a
+// member-by-member loop builds.  rc and msg hold a member's failure.
+struct MemberLevels {
+    std::vector<int64_t> lp[2];
+    std::vector<int32_t> le[2];
+    int rc = FBP_OK;
+    std::string msg;
+};
+
+void member_levels(const fbp_graph_desc *graphs, const std::vector<int32_t> &members, const std::vector<int> &halves,
+                   std::vector<MemberLevels> &out)
+{
+    const int32_t m = (int32_t)members.size();
+    out.assign(m, MemberLevels{});
+    std::atomic<int32_t> next{0};
+    auto work = [&] {
+        for (int32_t k; (k = next.fetch_add(1)) < m;) {
+            if (halves[k] == 0) continue;
+            const fbp_graph_desc &d = graphs[members[k]];
+            HostCSR h;
+            build_host_csr(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param, h);
+            for (int hf = 0; hf < halves[k]; ++hf) {
+                std::vector<int64_t> rank;
+                const int rc = build_ranks(h, d.schedule, hf, rank);
+                if (rc) {
+                    out[k].rc = rc;
+                    out[k].msg = fbp_last_error();  // this thread's message
+                    break;
+                }
+                dependency_levels(h, rank.data(), nullptr, h.ne, out[k].lp[hf], out[k].le[hf]);
+            }
+        }
+    };
+    const int threads = std::max(1, std::min<int>(host_threads_all(), m));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) {
+        try {
+            pool.emplace_back(work);
+        } catch (...) {  // no thread to be had: the others take its members
+            break;
+        }
+    }
+    work();
+    for (auto &th : pool) th.join();
 }
 
 int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_allocator *alloc)
@@ -164,30 +238,21 @@ int build_part(fbp_batch *b, int kind, const fbp_graph_desc *graphs, const fbp_a
     }
     // static parts: each member's own levels, merged by level index
     const int halves = kind == kStatic2 ? 2 : 1;
+    std::vector<MemberLevels> ml;
+    member_levels(graphs, P.members, std::vector<int>(m, halves), ml);
+    for (int32_t k = 0; k < m; ++k)
+        if (ml[k].rc) return fail(ml[k].rc, "batch graph %d: %s", P.members[k], ml[k].msg.c_str());
     std::vector<LevelSet> merged(halves);
     for (int hf = 0; hf < halves; ++hf) {
-        std::vector<std::vector<int64_t>> lps(m);
-        std::vector<std::vector<int32_t>> les(m);
         size_t nl = 0;
-        for (int32_t k = 0; k < m; ++k) {
-            const fbp_graph_desc &d = graphs[P.members[k]];
-            HostCSR h;
-            build_host_csr(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param, h);
-            std::vector<int64_t> rank;
-            rc = build_ranks(h, d.schedule, hf, rank);
-            if (rc) {
-                std::string msg = std::string("batch graph ") + std::to_string(P.members[k]) + ": " + fbp_last_error();
-                return fail(rc, "%s", msg.c_str());
-            }
-            dependency_levels(h, rank.data(), nullptr, h.ne, lps[k], les[k]);
-            nl = std::max(nl, lps[k].size() - 1);
-        }
+        for (int32_t k = 0; k < m; ++k) nl = std::max(nl, ml[k].lp[hf].size() - 1);
         LevelSet &ls = merged[hf];
         ls.lp.assign(1, 0);
         for (size_t L = 0; L < nl; ++L) {
             for (int32_t k = 0; k < m; ++k) {
-                if (L + 1 >= lps[k].size()) continue;
-                for (int64_t i = lps[k][L]; i < lps[k][L + 1]; ++i) ls.le.push_back(les[k][i] + P.edge_off[k]);
+                const std::vector<int64_t> &lpk = ml[k].lp[hf];
+                if (L + 1 >= lpk.size()) continue;
+                for (int64_t i = lpk[L]; i < lpk[L + 1]; ++i) ls.le.push_back(ml[k].le[hf][i] + P.edge_off[k]);
             }
             ls.lp.push_back((int64_t)ls.le.size());
         }
@@ -254,21 +319,17 @@ int build_queue_part(fbp_batch *b, const fbp_graph_desc *graphs, const fbp_alloc
     std::vector<int32_t> base[2] = {std::vector<int32_t>(m, 0), std::vector<int32_t>(m, 0)};
     std::vector<int32_t> count[2] = {std::vector<int32_t>(m, 0), std::vector<int32_t>(m, 0)};
     bool any_static = false;
+    std::vector<int> kinds(m);
+    for (int32_t k = 0; k < m; ++k) kinds[k] = P.mem[k].kind;
+    std::vector<MemberLevels> ml;
+    member_levels(graphs, P.members, kinds, ml);
     for (int32_t k = 0; k < m; ++k) {
         if (P.mem[k].kind == 0) continue;
         any_static = true;
-        const fbp_graph_desc &d = graphs[P.members[k]];
-        HostCSR h;
-        build_host_csr(d.n_vars, d.n_factors, d.factor_ptr, d.factor_vars, d.factor_type, d.factor_param, h);
+        if (ml[k].rc) return fail(ml[k].rc, "batch graph %d: %s", P.members[k], ml[k].msg.c_str());
         for (int hf = 0; hf < P.mem[k].kind; ++hf) {
-            std::vector<int64_t> rank, lpk;
-            std::vector<int32_t> lek;
-            rc = build_ranks(h, d.schedule, hf, rank);
-            if (rc) {
-                std::string msg = std::string("batch graph ") + std::to_string(P.members[k]) + ": " + fbp_last_error();
-                return fail(rc, "%s", msg.c_str());
-            }
-            dependency_levels(h, rank.data(), nullptr, h.ne, lpk, lek);
+            const std::vector<int64_t> &lpk = ml[k].lp[hf];
+            const std::vector<int32_t> &lek = ml[k].le[hf];
             base[hf][k] = (int32_t)lp[hf].size() - 1;
             count[hf][k] = (int32_t)lpk.size() - 1;
             for (size_t L = 0; L + 1 < lpk.size(); ++L) {
